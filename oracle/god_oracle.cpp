@@ -1,0 +1,596 @@
+// Genome-on-Diet seeding oracle: plain, single-threaded, obviously-correct C++.
+//
+// TEST INFRASTRUCTURE ONLY. Nothing in the product path may call, link or load
+// this file; only the tests, the smoke check and the CPU-baseline leg of the
+// benchmark use it. It shares no code, header or constant table with the CUDA
+// library: every step below is written from the paper's definitions, not from
+// the kernels.
+//
+// What it computes (section numbers are the paper's, arXiv 2211.08157):
+//   * sparsification of a sequence by a repeating 0/1 diet pattern, optionally
+//     shifted (Sec. 3 definitions of PR and PQ; Sec. 3.1 steps 1-2; Sec. 3.2);
+//   * 2-bit base codes with N breaking k-mers (Sec. 3.6.1);
+//   * double-strand (w,k)-minimizers of the patterned sequence with Thomas
+//     Wang's invertible integer hash over canonical k-mers (Sec. 3.1, Sec. 3.6.1);
+//   * the compressed seed index: sort, group by key, high-occurrence filter
+//     (Sec. 3.1 step 3, Sec. 3.2);
+//   * pattern alignment (Sec. 3.2) and compressed seeding to anchors (Sec. 3.3);
+//   * the learned-index (RMI) reference: MLP root forward/backward, leaf least
+//     squares and per-leaf error bounds in the same FP32 operation order the GPU
+//     lookup uses.
+//
+// Readings of points the paper leaves open are listed in the design notes; each
+// function below states the one it takes.
+//
+// Parity status: every function here is pinned by the CPU tests (brute force on
+// tiny inputs, closed forms, invariants, the paper's Fig. 3 example).
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <thread>
+#include <vector>
+
+namespace {
+
+// ---------------------------------------------------------------- encoding
+// Sec. 3: the alphabet is {A, C, G, T} plus the ambiguous base N.
+// Sec. 3.6.1: bases are coded in 2 bits; N is not coded and ends k-mers.
+// Every byte other than ACGT (either case) is treated as N.
+constexpr int kN = 4;
+int base_code(uint8_t c) {
+  switch (c) {
+    case 'A': case 'a': return 0;
+    case 'C': case 'c': return 1;
+    case 'G': case 'g': return 2;
+    case 'T': case 't': return 3;
+    default: return kN;
+  }
+}
+
+bool parse_pattern(const char* s, std::vector<int>& bits) {
+  bits.clear();
+  if (!s) return false;
+  bool any_one = false;
+  for (const char* c = s; *c; ++c) {
+    if (*c == '1') { bits.push_back(1); any_one = true; }
+    else if (*c == '0') bits.push_back(0);
+    else return false;
+  }
+  return !bits.empty() && any_one;
+}
+
+// ---------------------------------------------------------------- sparsify
+// Sec. 3 / Sec. 3.2: PQ_s keeps Q[i + s] wherever P[i mod p] = 1, i.e. base i of
+// the original sequence is kept under shift s iff i >= s and P[(i - s) mod p] = 1.
+// The reference uses s = 0. orig[j] is the original index of the j-th kept base.
+void sparsify(const uint8_t* seq, uint64_t len, const std::vector<int>& P, uint64_t s,
+              std::vector<int>& codes, std::vector<uint64_t>& orig) {
+  codes.clear();
+  orig.clear();
+  const uint64_t p = P.size();
+  for (uint64_t i = s; i < len; ++i) {
+    if (P[(i - s) % p]) {
+      codes.push_back(base_code(seq[i]));
+      orig.push_back(i);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- hash
+// Sec. 3.6.1 hashes every k-mer with Thomas Wang's integer hash (ref. [120]).
+// Wang's 64-bit mix is a chain of steps that are each a bijection on w-bit
+// integers: multiplication by an odd constant, or xor with a right shift of
+// itself. Restricted to 2k bits (everything reduced mod 2^(2k)) it stays a
+// permutation of [0, 4^k). Written here in its multiplicative form:
+//   x <- x * (2^21 - 1) - 1      (the "~x + (x << 21)" step)
+//   x <- x ^ (x >> 24)
+//   x <- x * 265                 (1 + 2^3 + 2^8)
+//   x <- x ^ (x >> 14)
+//   x <- x * 21                  (1 + 2^2 + 2^4)
+//   x <- x ^ (x >> 28)
+//   x <- x * (2^31 + 1)
+uint64_t wang_hash(uint64_t x, int k) {
+  const uint64_t mask = (k >= 32) ? ~0ULL : ((1ULL << (2 * k)) - 1);
+  x = (x * ((1ULL << 21) - 1) - 1) & mask;
+  x = x ^ (x >> 24);
+  x = (x * 265ULL) & mask;
+  x = x ^ (x >> 14);
+  x = (x * 21ULL) & mask;
+  x = x ^ (x >> 28);
+  x = (x * ((1ULL << 31) + 1)) & mask;
+  return x;
+}
+
+// ---------------------------------------------------------------- minimizers
+struct Mini {
+  uint64_t key;   // H(canonical k-mer code)
+  uint64_t pos;   // original index of the k-mer's first kept base
+  uint32_t z;     // 1 iff the reverse-complement code is the smaller one
+  uint64_t j;     // patterned index of the k-mer's first base
+};
+
+// Double-strand (w,k)-minimizers of one patterned sequence (Sec. 3.1, which
+// follows minimap2's definition; Sec. 3.6.1 for N handling).
+//   * k-mer j covers patterned bases j..j+k-1; it is usable iff none is N.
+//   * code: first base in the most significant 2 bits (A=0 C=1 G=2 T=3); the
+//     reverse complement reads the bases backwards with c -> 3 - c.
+//   * canonical = min(fwd, rc); z = [rc < fwd]; key = H(canonical).
+//   * fwd == rc (palindrome, even k only) keeps its window slot but is never
+//     chosen.
+//   * a window is w consecutive k-mer positions, all usable; every position
+//     whose key equals the window minimum is a minimizer; the result is the
+//     union over all windows (a set, reported in ascending j).
+std::vector<Mini> minimizers(const std::vector<int>& codes, const std::vector<uint64_t>& orig,
+                             int k, int w) {
+  std::vector<Mini> out;
+  const int64_t m = (int64_t)codes.size();
+  const int64_t nk = m - k + 1;
+  if (nk < w) return out;
+  std::vector<uint64_t> key(nk);
+  std::vector<uint32_t> z(nk);
+  std::vector<char> usable(nk), palin(nk);
+  for (int64_t j = 0; j < nk; ++j) {
+    bool ok = true;
+    uint64_t fwd = 0, rc = 0;
+    for (int t = 0; t < k; ++t) {
+      if (codes[j + t] == kN) { ok = false; break; }
+      fwd = fwd * 4 + (uint64_t)codes[j + t];
+    }
+    usable[j] = ok;
+    if (!ok) continue;
+    for (int t = k - 1; t >= 0; --t) rc = rc * 4 + (uint64_t)(3 - codes[j + t]);
+    palin[j] = (fwd == rc);
+    z[j] = rc < fwd ? 1u : 0u;
+    key[j] = wang_hash(std::min(fwd, rc), k);
+  }
+  std::vector<char> chosen(nk, 0);
+  for (int64_t i = 0; i + w <= nk; ++i) {
+    bool ok = true;
+    for (int64_t j = i; j < i + w; ++j) if (!usable[j]) { ok = false; break; }
+    if (!ok) continue;
+    bool have = false;
+    uint64_t mn = 0;
+    for (int64_t j = i; j < i + w; ++j) {
+      if (palin[j]) continue;
+      if (!have || key[j] < mn) { mn = key[j]; have = true; }
+    }
+    if (!have) continue;
+    for (int64_t j = i; j < i + w; ++j)
+      if (!palin[j] && key[j] == mn) chosen[j] = 1;
+  }
+  for (int64_t j = 0; j < nk; ++j)
+    if (chosen[j]) out.push_back(Mini{key[j], orig[j], z[j], (uint64_t)j});
+  return out;
+}
+
+std::vector<Mini> seq_minimizers(const uint8_t* seq, uint64_t len, const std::vector<int>& P,
+                                 uint64_t shift, int k, int w) {
+  std::vector<int> codes;
+  std::vector<uint64_t> orig;
+  sparsify(seq, len, P, shift, codes, orig);
+  return minimizers(codes, orig, k, w);
+}
+
+// ---------------------------------------------------------------- index
+// Sec. 3.1 step 3: minimizers of the patterned reference (shift 0) are appended
+// to an array, the array is sorted, and each key maps to the sorted list of
+// original start locations. Sec. 3.2: keys occurring too often are discarded;
+// one threshold is used everywhere: a key is kept iff its count <= max_occ.
+struct Index {
+  std::vector<int> P;
+  int k = 0, w = 0;
+  uint32_t max_occ = 0;
+  uint64_t n_minimizers = 0;           // before the filter
+  std::vector<uint64_t> keys;          // kept keys, ascending
+  std::vector<uint64_t> start;         // keys.size() + 1 offsets into ent
+  std::vector<uint64_t> ent;           // (pos << 1) | z, ascending within a key
+};
+
+struct Rec {
+  uint64_t key, pos;
+  uint32_t z;
+};
+
+Index* build_index(const uint8_t* ref, uint64_t len, const std::vector<int>& P, int k, int w,
+                   uint32_t max_occ) {
+  Index* idx = new Index();
+  idx->P = P;
+  idx->k = k;
+  idx->w = w;
+  idx->max_occ = max_occ;
+  std::vector<Mini> mins = seq_minimizers(ref, len, P, 0, k, w);
+  idx->n_minimizers = mins.size();
+  std::vector<Rec> recs;
+  recs.reserve(mins.size());
+  for (const Mini& m : mins) recs.push_back(Rec{m.key, m.pos, m.z});
+  std::sort(recs.begin(), recs.end(), [](const Rec& a, const Rec& b) {
+    if (a.key != b.key) return a.key < b.key;
+    if (a.pos != b.pos) return a.pos < b.pos;
+    return a.z < b.z;
+  });
+  idx->start.push_back(0);
+  size_t i = 0;
+  while (i < recs.size()) {
+    size_t e = i;
+    while (e < recs.size() && recs[e].key == recs[i].key) ++e;
+    const uint64_t count = e - i;
+    if (count <= max_occ) {
+      idx->keys.push_back(recs[i].key);
+      for (size_t t = i; t < e; ++t) idx->ent.push_back((recs[t].pos << 1) | recs[t].z);
+      idx->start.push_back(idx->ent.size());
+    }
+    i = e;
+  }
+  return idx;
+}
+
+// Number of index entries for key (0 when absent or filtered), and where they sit.
+uint64_t index_find(const Index* idx, uint64_t key, uint64_t* first) {
+  auto it = std::lower_bound(idx->keys.begin(), idx->keys.end(), key);
+  if (it == idx->keys.end() || *it != key) return 0;
+  const size_t r = (size_t)(it - idx->keys.begin());
+  if (first) *first = idx->start[r];
+  return idx->start[r + 1] - idx->start[r];
+}
+
+// ---------------------------------------------------------------- seeding
+struct Anchor {
+  uint32_t read_id, read_pos, ref_pos, strand;
+};
+
+// Sec. 3.2 pattern alignment for one read. For every shift s in [0, p): take the
+// minimizers of the read sparsified at s, keep the first t in ascending
+// patterned position (t = 0 keeps all), and sum the index counts of their keys
+// (a filtered or absent key counts 0; a key seen twice counts twice). The
+// alignment index a is the shift with the largest sum; the smallest such shift
+// wins ties, so a = 0 when every sum is 0.
+uint32_t pattern_align(const Index* idx, const uint8_t* read, uint64_t len, uint32_t t,
+                       std::vector<uint64_t>* sums_out) {
+  const uint32_t p = (uint32_t)idx->P.size();
+  uint64_t best = 0;
+  uint32_t a = 0;
+  for (uint32_t s = 0; s < p; ++s) {
+    std::vector<Mini> mins = seq_minimizers(read, len, idx->P, s, idx->k, idx->w);
+    const size_t use = (t == 0) ? mins.size() : std::min<size_t>(mins.size(), t);
+    uint64_t sum = 0;
+    for (size_t i = 0; i < use; ++i) sum += index_find(idx, mins[i].key, nullptr);
+    if (sums_out) sums_out->push_back(sum);
+    if (sum > best) { best = sum; a = s; }
+  }
+  return a;
+}
+
+// Sec. 3.3 compressed seeding for one read: minimizers of the read sparsified at
+// shift a, each looked up exactly; one anchor per index entry of a found key.
+// read_pos is the original index (shift included) of the read k-mer's first
+// kept base; strand = z_read xor z_ref.
+void seed_read(const Index* idx, uint32_t read_id, const uint8_t* read, uint64_t len, uint32_t a,
+               std::vector<Anchor>& out) {
+  std::vector<Mini> mins = seq_minimizers(read, len, idx->P, a, idx->k, idx->w);
+  for (const Mini& m : mins) {
+    uint64_t first = 0;
+    const uint64_t c = index_find(idx, m.key, &first);
+    for (uint64_t e = first; e < first + c; ++e) {
+      const uint64_t v = idx->ent[e];
+      out.push_back(Anchor{read_id, (uint32_t)m.pos, (uint32_t)(v >> 1),
+                           (uint32_t)((v & 1) ^ m.z)});
+    }
+  }
+}
+
+bool anchor_less(const Anchor& a, const Anchor& b) {
+  if (a.read_id != b.read_id) return a.read_id < b.read_id;
+  if (a.ref_pos != b.ref_pos) return a.ref_pos < b.ref_pos;
+  if (a.read_pos != b.read_pos) return a.read_pos < b.read_pos;
+  return a.strand < b.strand;
+}
+
+void seed_range(const Index* idx, const uint8_t* reads, const uint64_t* offsets, uint32_t lo,
+                uint32_t hi, uint32_t t, std::vector<Anchor>& out, uint32_t* shifts) {
+  for (uint32_t r = lo; r < hi; ++r) {
+    const uint8_t* q = reads + offsets[r];
+    const uint64_t len = offsets[r + 1] - offsets[r];
+    const uint32_t a = pattern_align(idx, q, len, t, nullptr);
+    if (shifts) shifts[r] = a;
+    seed_read(idx, r, q, len, a, out);
+  }
+}
+
+// ---------------------------------------------------------------- RMI reference
+// Learned index over the sorted kept keys: a root MLP 1 -> H -> 1 (ReLU) maps the
+// normalised key to a leaf; each leaf holds a linear model of the rank. The
+// FP32 evaluation below fixes the operation order (fused multiply-adds in index
+// order) so that error bounds computed here hold for any evaluator that uses
+// the same order.
+struct RootF32 {
+  int H;
+  const float* W1;
+  const float* b1;
+  const float* W2;
+  float b2;
+};
+
+float root_forward_f32(const RootF32& r, float x) {
+  float f = r.b2;
+  for (int h = 0; h < r.H; ++h) {
+    float a = std::fmaf(r.W1[h], x, r.b1[h]);
+    a = a > 0.0f ? a : 0.0f;
+    f = std::fmaf(r.W2[h], a, f);
+  }
+  return f;
+}
+
+// Normalised key: (key - kmin) as float, times inv_span (both FP32, nearest).
+float key_to_x(uint64_t key, uint64_t kmin, float inv_span) {
+  const float d = (float)(key - kmin);
+  return d * inv_span;
+}
+
+uint32_t leaf_of(const RootF32& r, uint64_t key, uint64_t kmin, float inv_span, uint32_t n_leaves) {
+  const float x = key_to_x(key, kmin, inv_span);
+  const float f = root_forward_f32(r, x);
+  const float s = f * (float)n_leaves;
+  if (!(s > 0.0f)) return 0;                       // also catches NaN
+  if (s >= (float)n_leaves) return n_leaves - 1;
+  return (uint32_t)std::floor(s);
+}
+
+// Leaf prediction of the rank: floor(fma(slope, (float)(key - base), icept)),
+// the difference taken as a signed 64-bit integer.
+int64_t leaf_predict(float slope, float icept, uint64_t base, uint64_t key) {
+  const float d = (float)(int64_t)(key - base);
+  const float v = std::fmaf(slope, d, icept);
+  if (!(v > -1.0e18f)) return INT64_MIN / 2;
+  if (v > 1.0e18f) return INT64_MAX / 2;
+  return (int64_t)std::floor(v);
+}
+
+}  // namespace
+
+// ======================================================================== C ABI
+extern "C" {
+
+// Sparsify `seq` under (pattern, shift). Writes kept 2-bit codes (4 = N) and
+// original indices into caller buffers of capacity `cap`. Returns the patterned
+// length, or -1 on a bad pattern.
+int64_t orc_sparsify(const uint8_t* seq, uint64_t len, const char* pattern, uint64_t shift,
+                     uint8_t* codes_out, uint64_t* orig_out, uint64_t cap) {
+  std::vector<int> P;
+  if (!parse_pattern(pattern, P)) return -1;
+  std::vector<int> codes;
+  std::vector<uint64_t> orig;
+  sparsify(seq, len, P, shift, codes, orig);
+  for (size_t i = 0; i < codes.size() && i < cap; ++i) {
+    if (codes_out) codes_out[i] = (uint8_t)codes[i];
+    if (orig_out) orig_out[i] = orig[i];
+  }
+  return (int64_t)codes.size();
+}
+
+void orc_hash_array(const uint64_t* x, uint64_t n, int k, uint64_t* out) {
+  for (uint64_t i = 0; i < n; ++i) out[i] = wang_hash(x[i], k);
+}
+
+// Minimizers of `seq` under (pattern, shift, k, w), ascending patterned index.
+// Returns the count; fills up to `cap` entries of each non-null output.
+int64_t orc_minimizers(const uint8_t* seq, uint64_t len, const char* pattern, uint64_t shift,
+                       int k, int w, uint64_t* keys, uint64_t* pos, uint32_t* z, uint64_t* jpat,
+                       uint64_t cap) {
+  std::vector<int> P;
+  if (!parse_pattern(pattern, P) || k < 1 || k > 28 || w < 1) return -1;
+  std::vector<Mini> mins = seq_minimizers(seq, len, P, shift, k, w);
+  for (size_t i = 0; i < mins.size() && i < cap; ++i) {
+    if (keys) keys[i] = mins[i].key;
+    if (pos) pos[i] = mins[i].pos;
+    if (z) z[i] = mins[i].z;
+    if (jpat) jpat[i] = mins[i].j;
+  }
+  return (int64_t)mins.size();
+}
+
+void* orc_build_index(const uint8_t* ref, uint64_t len, const char* pattern, int k, int w,
+                      uint32_t max_occ) {
+  std::vector<int> P;
+  if (!parse_pattern(pattern, P) || k < 1 || k > 28 || w < 1) return nullptr;
+  return build_index(ref, len, P, k, w, max_occ);
+}
+
+void orc_free_index(void* h) { delete static_cast<Index*>(h); }
+
+// Sizes: [0] minimizers before the filter, [1] kept keys, [2] kept entries.
+void orc_index_sizes(const void* h, uint64_t* out3) {
+  const Index* idx = static_cast<const Index*>(h);
+  out3[0] = idx->n_minimizers;
+  out3[1] = idx->keys.size();
+  out3[2] = idx->ent.size();
+}
+
+// Copies kept keys (n_keys), offsets (n_keys + 1) and entries (n_ent).
+void orc_index_dump(const void* h, uint64_t* keys, uint64_t* start, uint64_t* ent) {
+  const Index* idx = static_cast<const Index*>(h);
+  if (keys) std::memcpy(keys, idx->keys.data(), idx->keys.size() * 8);
+  if (start) std::memcpy(start, idx->start.data(), idx->start.size() * 8);
+  if (ent) std::memcpy(ent, idx->ent.data(), idx->ent.size() * 8);
+}
+
+void orc_index_count(const void* h, const uint64_t* keys, uint64_t n, uint64_t* counts) {
+  const Index* idx = static_cast<const Index*>(h);
+  for (uint64_t i = 0; i < n; ++i) counts[i] = index_find(idx, keys[i], nullptr);
+}
+
+// Pattern alignment of one read; writes the p per-shift sums into sums_out.
+uint32_t orc_pattern_align(const void* h, const uint8_t* read, uint64_t len, uint32_t t,
+                           uint64_t* sums_out) {
+  const Index* idx = static_cast<const Index*>(h);
+  std::vector<uint64_t> sums;
+  const uint32_t a = pattern_align(idx, read, len, t, &sums);
+  if (sums_out) for (size_t i = 0; i < sums.size(); ++i) sums_out[i] = sums[i];
+  return a;
+}
+
+// Seeds reads [0, n) (CSR byte offsets, n + 1 entries) with `n_threads` host
+// threads over contiguous read shards (1 = the plain single-threaded oracle).
+// Returns a malloc'ed array of 4*u32 anchors sorted by (read_id, ref_pos,
+// read_pos, strand) and its length; per-read alignment indices go to `shifts`.
+uint32_t* orc_seed(const void* h, const uint8_t* reads, const uint64_t* offsets, uint32_t n,
+                   uint32_t t, int n_threads, uint64_t* n_out, uint32_t* shifts) {
+  const Index* idx = static_cast<const Index*>(h);
+  if (n_threads < 1) n_threads = 1;
+  if ((uint32_t)n_threads > n) n_threads = n > 0 ? (int)n : 1;
+  std::vector<std::vector<Anchor>> parts(n_threads);
+  std::vector<std::thread> pool;
+  for (int i = 0; i < n_threads; ++i) {
+    const uint32_t lo = (uint32_t)((uint64_t)n * i / n_threads);
+    const uint32_t hi = (uint32_t)((uint64_t)n * (i + 1) / n_threads);
+    if (n_threads == 1) {
+      seed_range(idx, reads, offsets, lo, hi, t, parts[i], shifts);
+    } else {
+      pool.emplace_back([=, &parts]() { seed_range(idx, reads, offsets, lo, hi, t, parts[i], shifts); });
+    }
+  }
+  for (auto& th : pool) th.join();
+  std::vector<Anchor> all;
+  for (auto& v : parts) all.insert(all.end(), v.begin(), v.end());
+  std::sort(all.begin(), all.end(), anchor_less);
+  *n_out = all.size();
+  uint32_t* buf = (uint32_t*)std::malloc(std::max<size_t>(1, all.size()) * sizeof(Anchor));
+  if (!all.empty()) std::memcpy(buf, all.data(), all.size() * sizeof(Anchor));
+  return buf;
+}
+
+void orc_free(void* p) { std::free(p); }
+
+// ---- RMI reference -------------------------------------------------------
+
+// Double-precision forward, MSE loss and analytic gradient of the root over a
+// batch (x_i, y_i). Parameter layout: W1[H], b1[H], W2[H], b2. Returns the loss
+// L = mean((f(x) - y)^2); grad (3H + 1 entries) gets dL/dtheta.
+double orc_root_loss_grad_f64(const double* theta, int H, const double* x, const double* y,
+                              uint64_t n, double* grad) {
+  const double* W1 = theta;
+  const double* b1 = theta + H;
+  const double* W2 = theta + 2 * H;
+  const double b2 = theta[3 * H];
+  std::vector<double> g(3 * H + 1, 0.0);
+  double loss = 0.0;
+  std::vector<double> a(H);
+  for (uint64_t i = 0; i < n; ++i) {
+    double f = b2;
+    for (int h = 0; h < H; ++h) {
+      const double pre = W1[h] * x[i] + b1[h];
+      a[h] = pre > 0 ? pre : 0;
+      f += W2[h] * a[h];
+    }
+    const double e = f - y[i];
+    loss += e * e;
+    const double de = 2.0 * e / (double)n;
+    for (int h = 0; h < H; ++h) {
+      g[2 * H + h] += de * a[h];
+      if (a[h] > 0) {
+        const double dpre = de * W2[h];
+        g[h] += dpre * x[i];
+        g[H + h] += dpre;
+      }
+    }
+    g[3 * H] += de;
+  }
+  if (grad) for (int i = 0; i < 3 * H + 1; ++i) grad[i] = g[i];
+  return n ? loss / (double)n : 0.0;
+}
+
+// FP32, strictly sequential version: samples in index order, each sample's
+// contribution added in FP32. Same parameter layout.
+float orc_root_loss_grad_f32(const float* theta, int H, const float* x, const float* y,
+                             uint64_t n, float* grad) {
+  const float* W1 = theta;
+  const float* b1 = theta + H;
+  const float* W2 = theta + 2 * H;
+  const float b2 = theta[3 * H];
+  std::vector<float> g(3 * H + 1, 0.0f);
+  float loss = 0.0f;
+  std::vector<float> a(H);
+  const float inv_n = n ? 1.0f / (float)n : 0.0f;
+  for (uint64_t i = 0; i < n; ++i) {
+    float f = b2;
+    for (int h = 0; h < H; ++h) {
+      const float pre = std::fmaf(W1[h], x[i], b1[h]);
+      a[h] = pre > 0.0f ? pre : 0.0f;
+      f = std::fmaf(W2[h], a[h], f);
+    }
+    const float e = f - y[i];
+    loss += e * e;
+    const float de = 2.0f * e * inv_n;
+    for (int h = 0; h < H; ++h) {
+      g[2 * H + h] += de * a[h];
+      if (a[h] > 0.0f) {
+        const float dpre = de * W2[h];
+        g[h] += dpre * x[i];
+        g[H + h] += dpre;
+      }
+    }
+    g[3 * H] += de;
+  }
+  if (grad) for (int i = 0; i < 3 * H + 1; ++i) grad[i] = g[i];
+  return loss * inv_n;
+}
+
+// Root FP32 forward on keys: normalised x and the leaf each key is routed to.
+void orc_root_route(const float* theta, int H, const uint64_t* keys, uint64_t n, uint64_t kmin,
+                    float inv_span, uint32_t n_leaves, float* x_out, uint32_t* leaf_out) {
+  RootF32 r{H, theta, theta + H, theta + 2 * H, theta[3 * H]};
+  for (uint64_t i = 0; i < n; ++i) {
+    if (x_out) x_out[i] = key_to_x(keys[i], kmin, inv_span);
+    if (leaf_out) leaf_out[i] = leaf_of(r, keys[i], kmin, inv_span, n_leaves);
+  }
+}
+
+// Leaf models for sorted keys (rank = array index) routed by a fixed root:
+// per leaf, base = smallest routed key; slope/intercept = least squares of rank
+// on (key - base) in double, rounded to FP32 (a single key: slope 0, intercept
+// = its rank; an empty leaf: all zero); eps = max |rank - prediction| with the
+// FP32 prediction of leaf_predict.
+void orc_rmi_fit_leaves(const float* theta, int H, const uint64_t* keys, uint64_t n, uint64_t kmin,
+                        float inv_span, uint32_t n_leaves, float* slope, float* icept,
+                        uint64_t* base, uint32_t* eps) {
+  RootF32 r{H, theta, theta + H, theta + 2 * H, theta[3 * H]};
+  std::vector<uint32_t> leaf(n);
+  for (uint64_t i = 0; i < n; ++i) leaf[i] = leaf_of(r, keys[i], kmin, inv_span, n_leaves);
+  std::vector<uint64_t> cnt(n_leaves, 0), bmin(n_leaves, UINT64_MAX);
+  for (uint64_t i = 0; i < n; ++i) {
+    cnt[leaf[i]]++;
+    bmin[leaf[i]] = std::min(bmin[leaf[i]], keys[i]);
+  }
+  std::vector<double> sx(n_leaves, 0), sy(n_leaves, 0), sxx(n_leaves, 0), sxy(n_leaves, 0);
+  for (uint64_t i = 0; i < n; ++i) {
+    const uint32_t l = leaf[i];
+    const double dx = (double)(keys[i] - bmin[l]);
+    const double dy = (double)i;
+    sx[l] += dx; sy[l] += dy; sxx[l] += dx * dx; sxy[l] += dx * dy;
+  }
+  for (uint32_t l = 0; l < n_leaves; ++l) {
+    base[l] = cnt[l] ? bmin[l] : 0;
+    eps[l] = 0;
+    if (cnt[l] == 0) { slope[l] = 0; icept[l] = 0; continue; }
+    const double c = (double)cnt[l];
+    const double den = c * sxx[l] - sx[l] * sx[l];
+    double b = 0.0, a = sy[l] / c;
+    if (cnt[l] > 1 && den > 0) {
+      b = (c * sxy[l] - sx[l] * sy[l]) / den;
+      a = (sy[l] - b * sx[l]) / c;
+    }
+    slope[l] = (float)b;
+    icept[l] = (float)a;
+  }
+  for (uint64_t i = 0; i < n; ++i) {
+    const uint32_t l = leaf[i];
+    const int64_t pred = leaf_predict(slope[l], icept[l], base[l], keys[i]);
+    const int64_t err = pred > (int64_t)i ? pred - (int64_t)i : (int64_t)i - pred;
+    const uint64_t e = (uint64_t)err;
+    if (e > eps[l]) eps[l] = (uint32_t)std::min<uint64_t>(e, 0xFFFFFFFFu);
+  }
+}
+
+}  // extern "C"
