@@ -1,0 +1,416 @@
+#!/usr/bin/env python3
+"""Benchmark: read bases/s of Genome-on-Diet seeding on one GB300 (and N replicas).
+
+One step = one pass of the whole hot path over one synthetic batch: build the
+compressed seed index of the 100 Mbp reference (sparsify, 2-bit code, hash,
+minimizers, radix-sort index, filter, hash table; plus the learned index with
+its on-GPU root training when --index learned), then seed all 2,000,000
+150 bp reads in one batched pass (pattern alignment over both shifts, lookups,
+anchors, per-read sorted anchor lists). value = read bases / step time with
+the reference and reads already in HBM; e2e = the same step through the C ABI
+with pinned host buffers, H2D of the inputs and D2H of the anchors inside the
+timed region.
+
+Multi-GPU (torchrun): reads are independent, so every rank seeds its own batch
+(weak scaling) against its own copy of the index; no data-path collective.
+The reference arm (--impl reference) times the plain C++ oracle on the host.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2211_08157_gb300 import synth  # noqa: E402
+
+METRIC = "read bases/sec & anchors/sec on 1 GB300, learned vs hash index, bit-exact anchors"
+L2_BYTES = 129 * 1024 * 1024
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return out
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, fl in rows for i, v in enumerate(fl) if v.lower() == "active"})
+        out.update(sm_mhz=statistics.median(r[0] for r in rows), sm_max_mhz=max(r[1] for r in rows),
+                   reasons=reasons, samples=len(rows))
+        return out
+
+
+def make_workload(name: str, n_reads: int | None, rank: int):
+    wl = synth.WORKLOADS[name]
+    ref = wl.make_reference()
+    # rank r seeds its own batch: reads drawn from stream 2 + 10 r
+    reads, offs, _ = wl.make_reads(ref, n=n_reads, seed_stream=2 + 10 * rank)
+    return wl, ref, reads, offs
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    return ws, rank, local
+
+
+def dist_max(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def dist_sum(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def barrier(ws: int):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+def oracle_timing(wl, ref, reads, offs, sample_reads: int, threads: int):
+    """Oracle index build (single-threaded, whole reference) + oracle seeding of a
+    read sample over `threads` host threads; returns seconds for the full batch."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    idx = oracle.Index(ref, wl.pattern, wl.k, wl.w, wl.max_occ)
+    t_index = time.perf_counter() - t0
+    n = offs.size - 1
+    m = min(sample_reads, n)
+    sub_offs = offs[: m + 1]
+    sub = reads[: int(sub_offs[-1])]
+    t0 = time.perf_counter()
+    idx.seed(sub, sub_offs, wl.t, threads=threads)
+    t_seed = time.perf_counter() - t0
+    idx.close()
+    scale = n / m
+    return t_index, t_seed, scale, int(sub_offs[-1])
+
+
+def run_reference(args, ws, rank):
+    """The oracle as the reference arm: host cores, bounded sample per step."""
+    if rank != 0:
+        return
+    wl, ref, reads, offs = make_workload(args.workload, args.n_reads, 0)
+    import oracle
+    oracle.build()
+    threads = os.cpu_count() or 1
+    bases = float(offs[-1])
+    n = offs.size - 1
+    m = min(args.ref_sample_reads, n)
+    t0 = time.perf_counter()
+    idx = oracle.Index(ref, wl.pattern, wl.k, wl.w, wl.max_occ)
+    t_index = time.perf_counter() - t0
+    sub_offs = offs[: m + 1]
+    sub = reads[: int(sub_offs[-1])]
+    for _ in range(args.warmup):
+        idx.seed(sub, sub_offs, wl.t, threads=threads)
+    times = []
+    n_anchor_sample = 0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        a, _ = idx.seed(sub, sub_offs, wl.t, threads=threads)
+        times.append(time.perf_counter() - t0)
+        n_anchor_sample = a.size
+    t_seed = statistics.mean(times)
+    step_s = t_index + t_seed * n / m
+    value = bases / step_s
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "read bases/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8/u64 integer", "data": "synthetic",
+        "config": {"workload": wl.name, "reads": n, "read_bases": int(bases), "ref_bases": int(ref.size),
+                   "pattern": wl.pattern, "k": wl.k, "w": wl.w, "max_occ": wl.max_occ, "pa_t": wl.t},
+        "anchors_per_s": n_anchor_sample * (n / m) / step_s,
+        "cpu_baseline": {"value": value, "unit": "read bases/s", "cores": threads, "kind": "oracle",
+                         "sample": f"oracle index of the full {ref.size} bp reference (1 thread, {t_index:.1f} s) + "
+                                   f"oracle seeding of the first {m} of {n} reads per step over {threads} threads, "
+                                   f"scaled to the full batch"},
+        "e2e": {"value": value, "unit": "read bases/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--index", default="hash", choices=["hash", "learned"])
+    ap.add_argument("--workload", default="short_100mbp_2m")
+    ap.add_argument("--n-reads", type=int, default=None)
+    ap.add_argument("--cpu-sample-reads", type=int, default=200_000)
+    ap.add_argument("--ref-sample-reads", type=int, default=100_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-compare", action="store_true", help="skip the other index kind's seed-only line")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "gb300":
+        args.warmup = 3
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+
+    import torch
+    import paper_2211_08157_gb300 as god
+    torch.cuda.set_device(local)
+    god.load()
+    wl, ref, reads, offs = make_workload(args.workload, args.n_reads, rank)
+    n = offs.size - 1
+    bases = float(offs[-1])
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(dev)
+    d_ref = torch.from_numpy(ref).to(dev)
+    d_reads = torch.from_numpy(reads).to(dev)
+    d_offs = torch.from_numpy(offs.view(np.int64)).to(dev)
+    flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device=dev)
+    kind = god.GOD_INDEX_LEARNED if args.index == "learned" else god.GOD_INDEX_HASH
+    params = god.god_params_init(index_kind=kind, pa_t=wl.t)
+    cap = max(int(bases // 4), 1 << 20)
+    d_out = torch.empty((cap, 4), dtype=torch.int32, device=dev)
+
+    def step(out):
+        idx = god.god_build_index(d_ref, wl.pattern, wl.k, wl.w, wl.max_occ, params=params, stream=stream)
+        m = god.god_seed_into(idx, d_reads, d_offs, out, stream=stream)
+        idx.close()
+        return m
+
+    # warm-up (also sizes the output)
+    n_anchors = 0
+    for _ in range(args.warmup):
+        try:
+            n_anchors = step(d_out)
+        except god.GodError as e:
+            if e.rc != -5:
+                raise
+            cap *= 2
+            d_out = torch.empty((cap, 4), dtype=torch.int32, device=dev)
+            n_anchors = step(d_out)
+    torch.cuda.synchronize(dev)
+
+    # ---- timed region: K steps, L2 flushed between steps (untimed)
+    clocks = ClockSampler(local)
+    clocks.start()
+    god.god_prof_reset()
+    god.god_prof_enable(True)
+    launches0 = god.god_launch_count()
+    step_ms = []
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        stream.synchronize()
+        barrier(ws)
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        n_anchors = step(d_out)
+        e1.record(stream)
+        e1.synchronize()
+        torch.cuda.synchronize(dev)
+        barrier(ws)
+        step_ms.append(e0.elapsed_time(e1))
+    launches = god.god_launch_count() - launches0
+    god.god_prof_enable(False)
+    prof = god.god_prof_report()
+    clk = clocks.stop()
+    ms = statistics.mean(step_ms)
+    ms_max = dist_max(ms, ws)
+    total_bases = dist_sum(bases, ws)
+    total_anchors = dist_sum(float(n_anchors), ws)
+    value = total_bases / (ms_max / 1e3)
+
+    # ---- dominant kernel roofline (CUDA events on the library's stream)
+    hbm, peak_src = peaks()
+    top = max(prof.items(), key=lambda kv: kv[1][1])
+    tname, (tl, tms, tbytes, tunits) = top
+    roof = None
+    if tbytes > 0:
+        per_launch_s = (tms / tl) / 1e3
+        achieved = (tbytes / tl) / per_launch_s / 1e9
+        roof = {"kernel": tname, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": None, "peak_source": peak_src,
+                "bytes_per_launch": tbytes / tl, "ms_per_launch": tms / tl}
+    else:
+        roof = {"kernel": tname, "bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None,
+                "traffic": None, "peak_source": peak_src, "ms_per_launch": tms / tl}
+    sk = prof.get("sketch")
+    sketch_roof = None
+    if sk and sk[2] > 0:
+        a = (sk[2] / sk[0]) / ((sk[1] / sk[0]) / 1e3) / 1e9
+        sketch_roof = {"achieved": a, "frac": a / hbm, "ms_per_step": sk[1] / args.steps,
+                       "patterned_bases_per_s": sk[3] / (sk[1] / 1e3)}
+    kernels = {k: {"launches_per_step": v[0] / args.steps, "ms_per_step": v[1] / args.steps,
+                   "share": v[1] / sum(x[1] for x in prof.values())} for k, v in
+               sorted(prof.items(), key=lambda kv: -kv[1][1])}
+
+    # ---- seed-only throughput with a resident index (hash and learned)
+    seed_only = {}
+    if not args.no_compare:
+        for nm, kd in (("hash", god.GOD_INDEX_HASH), ("learned", god.GOD_INDEX_LEARNED)):
+            prm = god.god_params_init(index_kind=kd, pa_t=wl.t)
+            idx = god.god_build_index(d_ref, wl.pattern, wl.k, wl.w, wl.max_occ, params=prm, stream=stream)
+            god.god_seed_into(idx, d_reads, d_offs, d_out, stream=stream)
+            tt = []
+            for _ in range(3):
+                with torch.cuda.stream(stream):
+                    flush.zero_()
+                stream.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                god.god_seed_into(idx, d_reads, d_offs, d_out, stream=stream)
+                e1.record(stream)
+                e1.synchronize()
+                tt.append(e0.elapsed_time(e1))
+            info = idx.info
+            seed_only[nm] = {"read_bases_per_s": bases / (statistics.mean(tt) / 1e3),
+                             "ms": statistics.mean(tt)}
+            if nm == "learned":
+                seed_only[nm].update(rmi_mean_eps=info["rmi_mean_eps"], rmi_leaves=info["rmi_leaves"],
+                                     rmi_fallback_key_frac=info["rmi_fallback_key_frac"])
+            idx.close()
+
+    # ---- end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        h_ref = torch.from_numpy(ref).pin_memory()
+        h_reads = torch.from_numpy(reads).pin_memory()
+        h_offs = torch.from_numpy(offs.view(np.int64)).pin_memory()
+        h_out = torch.empty((max(n_anchors, 1) + 1024, 4), dtype=torch.int32).pin_memory()
+        ref_np, reads_np, offs_np = h_ref.numpy(), h_reads.numpy(), h_offs.numpy().view(np.uint64)
+        out_np = h_out.numpy()
+
+        def e2e_step():
+            idx = god.god_build_index(ref_np, wl.pattern, wl.k, wl.w, wl.max_occ, params=params, stream=stream)
+            m = god.god_seed_into(idx, reads_np, offs_np, out_np, stream=stream)
+            idx.close()
+            return m
+
+        e2e_step()
+        tt = []
+        for _ in range(max(2, min(args.steps, 3))):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            stream.synchronize()
+            t0 = time.perf_counter()
+            m = e2e_step()
+            tt.append(time.perf_counter() - t0)
+        e2e_s = dist_max(statistics.mean(tt), ws)
+        e2e = {"value": total_bases / e2e_s, "unit": "read bases/s",
+               "h2d_bytes_per_step": int(ref.nbytes + reads.nbytes + offs.nbytes),
+               "d2h_bytes_per_step": int(m * 16), "ms_per_step": e2e_s * 1e3}
+
+    # ---- CPU oracle baseline (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        t_index, t_seed, scale, sb = oracle_timing(wl, ref, reads, offs, args.cpu_sample_reads, threads)
+        full_s = t_index + t_seed * scale
+        cpu = {"value": bases / full_s, "unit": "read bases/s", "cores": threads, "kind": "oracle",
+               "sample": f"oracle index of the full {ref.size} bp reference on 1 thread ({t_index:.1f} s) + oracle "
+                         f"seeding of {min(args.cpu_sample_reads, n)} reads ({sb} bases) on {threads} threads "
+                         f"({t_seed:.1f} s), scaled to the {n}-read batch"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "read bases/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u8/u64 integer", "data": "synthetic",
+            "config": {"workload": wl.name, "reads_per_gpu": n, "read_bases_per_gpu": int(bases),
+                       "ref_bases": int(ref.size), "pattern": wl.pattern, "k": wl.k, "w": wl.w,
+                       "max_occ": wl.max_occ, "pa_t": wl.t, "index": args.index,
+                       "step": "index build + batched seeding of all reads",
+                       "l2": "flushed between timed steps (256 MiB write); inputs 400 MB > L2",
+                       "parallelism": f"replicas x{ws}"},
+            "anchors_per_s": total_anchors / (ms_max / 1e3), "anchors_per_step": int(total_anchors),
+            "gpu_launches": int(launches),
+            "roofline": roof, "sketch_roofline": sketch_roof, "kernels": kernels,
+            "seed_only_resident_index": seed_only, "e2e": e2e, "cpu_baseline": cpu, "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

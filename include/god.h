@@ -1,0 +1,252 @@
+/*
+ * god.h - C ABI of the GB300 Genome-on-Diet seeding library (libgod.so).
+ *
+ * The library runs the data-parallel hot path of sparsified read mapping
+ * (Alser, Eudine & Mutlu, "Genome-on-Diet", arXiv 2211.08157) on one GPU:
+ *   - sparsify a sequence with a repeating 0/1 diet pattern (Sec. 3, Sec. 3.1
+ *     steps 1-2; shifted patterns in Sec. 3.2),
+ *   - 2-bit code the kept bases, N breaking k-mers (Sec. 3.6.1),
+ *   - double-strand (w,k)-minimizers with Thomas Wang's integer hash of the
+ *     canonical k-mer (Sec. 3.1, Sec. 3.6.1),
+ *   - a compressed seed index of the patterned reference with a
+ *     high-occurrence filter (Sec. 3.1 step 3, Sec. 3.2),
+ *   - pattern alignment of every read (Sec. 3.2) and compressed seeding that
+ *     turns the read's minimizers into anchors (Sec. 3.3),
+ *   - the anchors of each read sorted, as the voting step expects (Sec. 3.4
+ *     step 2).
+ * A learned index (a root MLP over the key plus linear leaves with per-leaf
+ * error bounds) can replace the hash table for lookup; it returns exactly the
+ * hash table's answers.
+ *
+ * Conventions for every entry point:
+ *   - Return value: GOD_OK (0) or a negative GOD_E* code. Nothing aborts or
+ *     traps; god_last_error() gives a message for the calling thread.
+ *   - Pointers: "host or device" inputs are classified with
+ *     cudaPointerGetAttributes; host inputs are copied to the device inside the
+ *     call. Inputs are borrowed and never retained after the call returns.
+ *   - Streams: `stream` is a cudaStream_t passed as void* (NULL = the legacy
+ *     default stream). Calls that return host results synchronise `stream`.
+ *   - Threads: an index is read-only after it is built; concurrent god_seed*
+ *     calls on one index are safe when each uses its own stream.
+ *   - Device: every call works on the CUDA device that is current on the
+ *     calling thread; an index must be used on the device it was built on.
+ */
+#ifndef GOD_H
+#define GOD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ----------------------------------------------------------------- errors */
+#define GOD_OK 0
+#define GOD_EINVAL -1   /* bad argument: pattern, k, w, sizes, offsets */
+#define GOD_ENOMEM -2   /* device or host allocation failed, or admission refused */
+#define GOD_ECUDA -3    /* a CUDA runtime error; god_last_error() has its text */
+#define GOD_ETIMEOUT -4 /* a bounded device-side wait gave up */
+#define GOD_ERANGE -5   /* caller buffer too small; the needed size is returned */
+#define GOD_EBUSY -6    /* serving: request not finished yet */
+
+const char *god_strerror(int rc);
+/* Message of the last failing call on this thread ("" if none). */
+const char *god_last_error(void);
+
+/* ----------------------------------------------------------------- types */
+typedef struct god_index god_index; /* opaque; owns its device memory */
+
+/* One anchor: a read minimizer matched to one index entry (Sec. 3.3).
+ * read_pos / ref_pos are original (unpatterned) 0-based positions of the
+ * first kept base of the k-mer; strand = z_read xor z_ref, where z = 1 when the
+ * reverse-complement k-mer is the canonical one. 16 bytes, 4 x u32 little
+ * endian. Lists are sorted by (read_id, ref_pos, read_pos, strand). */
+typedef struct {
+  uint32_t read_id, read_pos, ref_pos, strand;
+} god_anchor;
+
+#define GOD_INDEX_HASH 0    /* open-addressing hash table (default) */
+#define GOD_INDEX_LEARNED 1 /* learned index, hash table as fallback */
+
+#define GOD_ROOT_MLP 0      /* root = 1 -> 32 -> 1 ReLU MLP trained on the GPU */
+#define GOD_ROOT_UNTRAINED 1 /* the same MLP at its initialisation, not trained (ablation) */
+#define GOD_ROOT_LINEAR 2    /* no network: leaf = floor(x * leaves), x = normalised key (ablation) */
+
+typedef struct {
+  int index_kind;          /* GOD_INDEX_HASH or GOD_INDEX_LEARNED */
+  uint32_t pa_t;           /* pattern alignment: first t minimizers per shift (Sec. 3.2); 0 = all. Default 32 */
+  int rmi_leaf_bits;       /* learned index: 2^bits leaves, 16..20; 0 = chosen from the key count */
+  uint32_t rmi_eps_max;    /* leaves whose error bound exceeds this use the hash table; <= 255. Default 64 */
+  int rmi_root;            /* GOD_ROOT_MLP, GOD_ROOT_UNTRAINED or GOD_ROOT_LINEAR */
+  int rmi_train_steps;     /* Adam steps for the root; default 400 */
+  uint32_t rmi_train_samples; /* keys sampled for root training; default 65536 */
+  int tune;                /* 1 = autotune the sketch launch (cached per shape); 0 = fixed default */
+} god_params;
+
+/* Fills `p` with the defaults above. */
+void god_params_init(god_params *p);
+
+/* ----------------------------------------------------------------- index
+ * god_build_index: compressed indexing (Sec. 3.1): sparsify `ref` (len bytes,
+ * ASCII; any byte outside ACGTacgt is N) with `pattern` at shift 0, compute its
+ * (w,k)-minimizers, sort them by (key, position), and keep every key seen at
+ * most `max_occ` times (Sec. 3.2 filter). Builds the hash table, and the learned
+ * index when params->index_kind says so.
+ *   ref      host or device, len bytes; len < 2^32.
+ *   pattern  NUL-terminated string of '0'/'1', 1..64 characters, at least one '1'.
+ *   k        1..28;  w  1..255;  max_occ >= 1.
+ *   out      receives the index; release it with god_free.
+ * Errors: GOD_EINVAL for bad arguments, GOD_ENOMEM, GOD_ECUDA, GOD_ETIMEOUT.
+ */
+int god_build_index(const uint8_t *ref, uint64_t len, const char *pattern, int k, int w,
+                    uint32_t max_occ, god_index **out);
+int god_build_index_ex(const uint8_t *ref, uint64_t len, const char *pattern, int k, int w,
+                       uint32_t max_occ, const god_params *params, void *stream, god_index **out);
+
+typedef struct {
+  uint64_t ref_len;
+  uint64_t n_minimizers;   /* reference minimizers before the filter */
+  uint64_t n_keys;         /* distinct keys kept */
+  uint64_t n_entries;      /* (position, strand) entries of kept keys */
+  uint64_t ht_capacity;    /* hash-table slots (power of two) */
+  int k, w, p, x;          /* seed length, window, pattern length, pattern weight */
+  uint32_t max_occ;
+  int has_learned;         /* 1 when the learned index was built */
+  uint32_t rmi_leaves;     /* number of leaves */
+  uint32_t rmi_fallback_leaves; /* leaves routed to the hash table (error bound too large or empty) */
+  double rmi_mean_eps;     /* mean error bound over keys (key-weighted) */
+  uint32_t rmi_max_eps;    /* largest bound among leaves that do not fall back */
+  double rmi_fallback_key_frac; /* share of keys whose leaf falls back */
+  float rmi_final_loss;    /* root training loss (MSE on normalised rank) */
+  uint64_t device_bytes;   /* device memory held by the index */
+} god_index_info;
+
+int god_index_get_info(const god_index *idx, god_index_info *info);
+
+/* Copies the filtered index to host buffers (any may be NULL):
+ * keys[n_keys] ascending; start[n_keys + 1] offsets into entries;
+ * entries[n_entries] = (ref_pos << 1) | z, ascending within a key. */
+int god_index_export(const god_index *idx, uint64_t *keys, uint64_t *start, uint64_t *entries);
+
+/* Exact lookup of n keys (host or device) through the hash table (via = 0) or
+ * the learned index (via = 1). count[i] = index entries of keys[i] (0 when
+ * absent or filtered), first[i] = offset of the first entry. Output buffers
+ * are host or device, like the input. */
+int god_index_lookup(const god_index *idx, const uint64_t *keys, uint64_t n, int via,
+                     uint32_t *count, uint64_t *first, void *stream);
+
+/* ----------------------------------------------------------------- seeding
+ * god_seed: pattern alignment (Sec. 3.2) and compressed seeding (Sec. 3.3) of
+ * n reads against `idx`, all reads in one batched pass.
+ *   reads    host or device, the reads' bytes back to back.
+ *   offsets  host or device, n + 1 uint64 byte offsets (CSR; non-decreasing,
+ *            offsets[n] <= bytes in `reads`, each read < 2^31 bytes).
+ *   anchors  receives a malloc'ed host array of *n_anchors anchors, sorted by
+ *            (read_id, ref_pos, read_pos, strand); release with god_free.
+ * For each read and each shift s < p the first t minimizers of the read
+ * sparsified at s are looked up; their index counts are summed, and the shift
+ * with the largest sum (the smallest such shift on ties, 0 if all are 0) is the
+ * read's alignment index a. Every minimizer of the read sparsified at a whose
+ * key is kept in the index gives one anchor per index entry.
+ */
+int god_seed(const god_index *idx, const uint8_t *reads, const uint64_t *offsets, uint32_t n,
+             god_anchor **anchors, uint64_t *n_anchors);
+
+typedef struct {
+  void *stream;            /* cudaStream_t; NULL = legacy default stream */
+  uint32_t pa_t;           /* overrides the index's t when != UINT32_MAX */
+  int via;                 /* -1 = the index's kind, 0 = hash, 1 = learned */
+  uint32_t *shifts_out;    /* optional host/device array of n alignment indices */
+} god_seed_opts;
+
+void god_seed_opts_init(god_seed_opts *o);
+
+/* As god_seed, writing into a caller buffer `out` (host or device) of `cap`
+ * anchors. When cap is too small nothing is written, *n_anchors gets the
+ * needed count and GOD_ERANGE is returned. Device outputs are complete when
+ * the call returns (the stream is synchronised). */
+int god_seed_into(const god_index *idx, const uint8_t *reads, const uint64_t *offsets, uint32_t n,
+                  god_anchor *out, uint64_t cap, uint64_t *n_anchors, const god_seed_opts *opts);
+
+/* Device-resident variant: inputs on the device, the anchor array allocated on
+ * the device (stream-ordered on opts->stream); release with god_free. */
+int god_seed_device(const god_index *idx, const uint8_t *d_reads, const uint64_t *d_offsets,
+                    uint32_t n, god_anchor **d_anchors, uint64_t *n_anchors, const god_seed_opts *opts);
+
+/* ----------------------------------------------------------------- sketch
+ * Minimizers of one sequence sparsified with (pattern, shift) (Sec. 3.1,
+ * Sec. 3.6.1), in ascending patterned position: key, original position of the
+ * k-mer's first kept base, strand bit z. `seq` host or device; outputs host or
+ * device buffers of `cap` entries (any may be NULL). *n_out = the count; when
+ * cap is too small GOD_ERANGE is returned and nothing is written. */
+int god_sketch(const uint8_t *seq, uint64_t len, const char *pattern, uint32_t shift, int k, int w,
+               uint64_t *keys, uint32_t *pos, uint8_t *z, uint64_t cap, uint64_t *n_out, void *stream);
+
+/* ----------------------------------------------------------------- learned index
+ * Gradient of the root MLP's mean squared error (1 -> H -> 1, ReLU; parameter
+ * layout W1[H], b1[H], W2[H], b2) over samples (x[i], y[i]), computed by the
+ * GPU training kernels. All arrays are host. Returns the loss in *loss. */
+int god_rmi_root_grad(const float *theta, int H, const float *x, const float *y, uint64_t n,
+                      float *grad, float *loss);
+
+/* ----------------------------------------------------------------- memory
+ * Releases an index, or an anchor array returned by god_seed / god_seed_device.
+ * NULL is ignored. Device arrays are freed stream-ordered on the stream they
+ * were allocated on. */
+void god_free(void *p);
+
+/* Kernels launched by this library in this process so far. */
+uint64_t god_launch_count(void);
+
+/* Opt-in kernel timing: while enabled, every launch is bracketed by a pair of
+ * CUDA events on its stream. god_prof_report writes a JSON object
+ * {"kernel": [launches, total_ms, algorithmic_bytes, units], ...} (bytes and
+ * units are filled in for the sketch kernel: patterned bases read plus 16-byte
+ * minimizer records written; and for the lookups: 32 bytes per probe) of
+ * everything timed since the last
+ * reset into buf (NUL-terminated) and returns 0, or returns the needed size
+ * when cap is too small. Reading the report waits for the timed launches. */
+void god_prof_enable(int on);
+void god_prof_reset(void);
+int god_prof_report(char *buf, uint64_t cap);
+
+/* ----------------------------------------------------------------- serving
+ * A continuous-batching server over one resident index: requests (read
+ * batches) are queued, admitted into free slots while device memory allows,
+ * merged with other waiting requests into one batched seeding pass, and run
+ * concurrently on per-slot streams. Results are per-request host arrays.
+ */
+typedef struct god_server god_server;
+
+typedef struct {
+  int slots;               /* concurrent batches on the device (streams); default 4 */
+  uint64_t mem_budget;     /* device bytes the server may hold for batches; 0 = 80% of free memory */
+  uint64_t max_batch_bases;/* bases merged into one pass at most; default 64 Mi */
+} god_server_config;
+
+void god_server_config_init(god_server_config *c);
+int god_server_create(const god_index *idx, const god_server_config *cfg, god_server **out);
+/* Queues a copy of the reads (host) and returns a request id. */
+int god_server_submit(god_server *s, const uint8_t *reads, const uint64_t *offsets, uint32_t n,
+                      uint64_t *request_id);
+/* Waits up to timeout_ms (negative = forever) for a request. On GOD_OK the
+ * anchors (read_id local to the request) are returned as a malloc'ed host
+ * array (release with god_free) and, if latency_s is not NULL, the time from
+ * submit to completion; GOD_EBUSY if it is not done in time. A request that
+ * alone exceeds the memory budget completes with GOD_ENOMEM. */
+int god_server_wait(god_server *s, uint64_t request_id, int timeout_ms, god_anchor **anchors,
+                    uint64_t *n_anchors, double *latency_s);
+
+typedef struct {
+  uint64_t submitted, completed, batches, max_inflight_batches, merged_requests;
+  uint64_t rejected;       /* requests larger than the memory budget */
+} god_server_stats;
+
+int god_server_get_stats(god_server *s, god_server_stats *st);
+int god_server_destroy(god_server *s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GOD_H */

@@ -1,0 +1,300 @@
+"""GB300-native Genome-on-Diet seeding (arXiv 2211.08157): Python binding.
+
+A thin ctypes layer over ``libgod.so`` whose functions carry the C ABI's names
+(include/god.h) and only marshal arguments: every step of the path runs in the
+library's CUDA kernels. Host inputs are numpy arrays (or bytes); device inputs
+are torch CUDA tensors (PyTorch provides device memory and streams only).
+There is no CPU fallback: a missing or unloadable library raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib
+from ._lib import GodError, IndexInfo, Params, SeedOpts, ServerConfig, ServerStats, build, check, load
+
+ANCHOR_DTYPE = np.dtype([("read_id", "<u4"), ("read_pos", "<u4"), ("ref_pos", "<u4"), ("strand", "<u4")])
+
+GOD_INDEX_HASH, GOD_INDEX_LEARNED = 0, 1
+GOD_ROOT_MLP, GOD_ROOT_UNTRAINED, GOD_ROOT_LINEAR = 0, 1, 2
+
+
+def _ptr(x):
+    """Address of a numpy array, bytes object or torch tensor."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be contiguous")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    raise TypeError(f"unsupported buffer {type(x)}")
+
+
+def _u8(x):
+    if isinstance(x, (bytes, bytearray)):
+        return np.frombuffer(bytes(x), dtype=np.uint8)
+    return x
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def god_params_init(**overrides) -> Params:
+    p = Params()
+    load().god_params_init(C.byref(p))
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+class GodIndex:
+    """Owns a ``god_index*``; released with god_free when closed or collected."""
+
+    def __init__(self, handle: int):
+        self.h = C.c_void_p(handle)
+
+    def close(self):
+        if self.h and self.h.value:
+            load().god_free(self.h)
+            self.h = C.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def info(self) -> dict:
+        return god_index_get_info(self)
+
+
+def god_build_index(ref, pattern: str, k: int, w: int, max_occ: int, params: Params | None = None,
+                    stream=None) -> GodIndex:
+    ref = _u8(ref)
+    n = ref.size if isinstance(ref, np.ndarray) else ref.numel()
+    out = C.c_void_p()
+    L = load()
+    if params is None:
+        check(L.god_build_index(_ptr(ref), n, pattern.encode(), k, w, max_occ, C.byref(out)))
+    else:
+        check(L.god_build_index_ex(_ptr(ref), n, pattern.encode(), k, w, max_occ, C.byref(params),
+                                   _stream_ptr(stream), C.byref(out)))
+    return GodIndex(out.value)
+
+
+def god_index_get_info(index: GodIndex) -> dict:
+    info = IndexInfo()
+    check(load().god_index_get_info(index.h, C.byref(info)))
+    return {name: getattr(info, name) for name, _ in IndexInfo._fields_}
+
+
+def god_index_export(index: GodIndex):
+    info = god_index_get_info(index)
+    keys = np.zeros(max(info["n_keys"], 1), np.uint64)
+    start = np.zeros(info["n_keys"] + 1, np.uint64)
+    ent = np.zeros(max(info["n_entries"], 1), np.uint64)
+    check(load().god_index_export(index.h, _ptr(keys), _ptr(start), _ptr(ent)))
+    return keys[: info["n_keys"]], start, ent[: info["n_entries"]]
+
+
+def god_index_lookup(index: GodIndex, keys, via: int = 0, stream=None):
+    keys = np.ascontiguousarray(keys, dtype=np.uint64) if isinstance(keys, (np.ndarray, list)) else keys
+    n = keys.size if isinstance(keys, np.ndarray) else keys.numel()
+    if isinstance(keys, np.ndarray):
+        count = np.zeros(n, np.uint32)
+        first = np.zeros(n, np.uint64)
+    else:
+        import torch
+        count = torch.zeros(n, dtype=torch.int32, device=keys.device)
+        first = torch.zeros(n, dtype=torch.int64, device=keys.device)
+    check(load().god_index_lookup(index.h, _ptr(keys), n, via, _ptr(count), _ptr(first), _stream_ptr(stream)))
+    return count, first
+
+
+def _opts(stream=None, pa_t=None, via=None, shifts_out=None) -> SeedOpts:
+    o = SeedOpts()
+    load().god_seed_opts_init(C.byref(o))
+    o.stream = _stream_ptr(stream)
+    if pa_t is not None:
+        o.pa_t = pa_t
+    if via is not None:
+        o.via = via
+    o.shifts_out = _ptr(shifts_out)
+    return o
+
+
+def god_seed(index: GodIndex, reads, offsets):
+    """Sorted anchors of a read batch (host numpy arrays in, structured array out)."""
+    reads = _u8(reads)
+    offs = np.ascontiguousarray(offsets, dtype=np.uint64) if isinstance(offsets, np.ndarray) else offsets
+    n = (offs.size if isinstance(offs, np.ndarray) else offs.numel()) - 1
+    ptr = C.c_void_p()
+    cnt = C.c_uint64()
+    L = load()
+    check(L.god_seed(index.h, _ptr(reads), _ptr(offs), n, C.byref(ptr), C.byref(cnt)))
+    m = cnt.value
+    try:
+        if m:
+            buf = (C.c_uint32 * (4 * m)).from_address(ptr.value)
+            arr = np.frombuffer(buf, dtype=np.uint32).copy()
+        else:
+            arr = np.zeros(0, np.uint32)
+    finally:
+        L.god_free(ptr)
+    return arr.view(ANCHOR_DTYPE)
+
+
+def god_seed_into(index: GodIndex, reads, offsets, out, stream=None, pa_t=None, via=None, shifts_out=None) -> int:
+    """Anchors written into `out` (host numpy or device tensor of 16-byte rows); returns the count.
+    Raises GodError(rc=GOD_ERANGE) with the needed count when `out` is too small."""
+    reads = _u8(reads)
+    n = (offsets.size if isinstance(offsets, np.ndarray) else offsets.numel()) - 1
+    cap = (out.nbytes if isinstance(out, np.ndarray) else out.numel() * out.element_size()) // 16
+    cnt = C.c_uint64()
+    o = _opts(stream, pa_t, via, shifts_out)
+    rc = load().god_seed_into(index.h, _ptr(reads), _ptr(offsets), n, _ptr(out), cap, C.byref(cnt), C.byref(o))
+    if rc == -5:
+        err = GodError(rc, f"output holds {cap} anchors, {cnt.value} needed")
+        err.needed = cnt.value
+        raise err
+    check(rc)
+    return cnt.value
+
+
+def god_seed_device(index: GodIndex, d_reads, d_offsets, stream=None, pa_t=None, via=None, shifts_out=None):
+    """Device inputs (torch CUDA tensors) -> (device pointer, count); free with god_free."""
+    n = d_offsets.numel() - 1
+    ptr = C.c_void_p()
+    cnt = C.c_uint64()
+    o = _opts(stream, pa_t, via, shifts_out)
+    check(load().god_seed_device(index.h, _ptr(d_reads), _ptr(d_offsets), n, C.byref(ptr), C.byref(cnt),
+                                 C.byref(o)))
+    return ptr.value, cnt.value
+
+
+def god_sketch(seq, pattern: str, shift: int, k: int, w: int, stream=None):
+    """(keys, original positions, z) of the minimizers of one sequence."""
+    seq = _u8(seq)
+    n = seq.size if isinstance(seq, np.ndarray) else seq.numel()
+    cnt = C.c_uint64()
+    L = load()
+    rc = L.god_sketch(_ptr(seq), n, pattern.encode(), shift, k, w, None, None, None, 0, C.byref(cnt),
+                      _stream_ptr(stream))
+    if rc not in (0, -5):
+        check(rc)
+    m = cnt.value
+    keys = np.zeros(max(m, 1), np.uint64)
+    pos = np.zeros(max(m, 1), np.uint32)
+    z = np.zeros(max(m, 1), np.uint8)
+    check(L.god_sketch(_ptr(seq), n, pattern.encode(), shift, k, w, _ptr(keys), _ptr(pos), _ptr(z), m,
+                       C.byref(cnt), _stream_ptr(stream)))
+    return keys[:m], pos[:m], z[:m]
+
+
+def god_rmi_root_grad(theta, H: int, x, y):
+    th = np.ascontiguousarray(theta, np.float32)
+    xs = np.ascontiguousarray(x, np.float32)
+    ys = np.ascontiguousarray(y, np.float32)
+    g = np.zeros(3 * H + 1, np.float32)
+    loss = np.zeros(1, np.float32)
+    check(load().god_rmi_root_grad(_ptr(th), H, _ptr(xs), _ptr(ys), xs.size, _ptr(g), _ptr(loss)))
+    return float(loss[0]), g
+
+
+def god_free(ptr):
+    load().god_free(C.c_void_p(ptr) if isinstance(ptr, int) else ptr)
+
+
+def god_launch_count() -> int:
+    return int(load().god_launch_count())
+
+
+def god_prof_enable(on: bool = True):
+    load().god_prof_enable(1 if on else 0)
+
+
+def god_prof_reset():
+    load().god_prof_reset()
+
+
+def god_prof_report() -> dict:
+    """{kernel name: (launches, total ms, algorithmic bytes, units)} timed with CUDA events."""
+    import json
+    L = load()
+    need = L.god_prof_report(None, 0)
+    buf = C.create_string_buffer(max(need, 2) + 64)
+    rc = L.god_prof_report(buf, len(buf))
+    if rc != 0:
+        raise RuntimeError("profile report buffer too small")
+    return {k: (int(v[0]), float(v[1]), float(v[2]), float(v[3])) for k, v in json.loads(buf.value.decode()).items()}
+
+
+# ---------------------------------------------------------------- serving
+class GodServer:
+    def __init__(self, index: GodIndex, slots: int = 4, mem_budget: int = 0, max_batch_bases: int = 0):
+        L = load()
+        cfg = ServerConfig()
+        L.god_server_config_init(C.byref(cfg))
+        cfg.slots = slots
+        if mem_budget:
+            cfg.mem_budget = mem_budget
+        if max_batch_bases:
+            cfg.max_batch_bases = max_batch_bases
+        h = C.c_void_p()
+        check(L.god_server_create(index.h, C.byref(cfg), C.byref(h)))
+        self.h = h
+        self.index = index
+
+    def submit(self, reads, offsets) -> int:
+        reads = _u8(reads)
+        offs = np.ascontiguousarray(offsets, dtype=np.uint64)
+        rid = C.c_uint64()
+        check(load().god_server_submit(self.h, _ptr(reads), _ptr(offs), offs.size - 1, C.byref(rid)))
+        return rid.value
+
+    def wait(self, request_id: int, timeout_ms: int = -1, with_latency: bool = False):
+        ptr = C.c_void_p()
+        cnt = C.c_uint64()
+        lat = C.c_double()
+        L = load()
+        rc = L.god_server_wait(self.h, request_id, timeout_ms, C.byref(ptr), C.byref(cnt), C.byref(lat))
+        if rc == -6:
+            return None
+        check(rc)
+        m = cnt.value
+        try:
+            arr = np.frombuffer((C.c_uint32 * (4 * m)).from_address(ptr.value), dtype=np.uint32).copy() if m \
+                else np.zeros(0, np.uint32)
+        finally:
+            L.god_free(ptr)
+        if with_latency:
+            return arr.view(ANCHOR_DTYPE), lat.value
+        return arr.view(ANCHOR_DTYPE)
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        check(load().god_server_get_stats(self.h, C.byref(s)))
+        return {name: getattr(s, name) for name, _ in ServerStats._fields_}
+
+    def close(self):
+        if self.h and self.h.value:
+            check(load().god_server_destroy(self.h))
+            self.h = C.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,237 @@
+// Internal declarations shared by the CUDA translation units of libgod.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <string>
+
+#include "../../include/god.h"
+
+namespace god {
+
+// ------------------------------------------------------------------ errors
+void set_error(const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+
+#define GOD_CK(call)                                                        \
+  do {                                                                      \
+    cudaError_t _e = (call);                                                \
+    if (_e != cudaSuccess) return ::god::cuda_fail(_e, #call, __FILE__, __LINE__); \
+  } while (0)
+
+#define GOD_TRY(call)                 \
+  do {                                \
+    int _rc = (call);                 \
+    if (_rc != GOD_OK) return _rc;    \
+  } while (0)
+
+extern std::atomic<uint64_t> g_launches;
+extern std::atomic<int> g_prof_on;
+// Opt-in per-kernel timing: an event pair around each launch, resolved later.
+void prof_begin(cudaStream_t st, cudaEvent_t* a);
+void prof_end(const char* name, cudaStream_t st, cudaEvent_t a);
+// Adds algorithmic bytes (and processed units) to a kernel's profile entry.
+void prof_add_work(const char* name, double bytes, double units);
+
+// Every kernel launch goes through this macro: it counts the launch, times it
+// when profiling is on, and turns a launch failure into GOD_ECUDA.
+#define GOD_LAUNCH(kernel, grid, block, smem, stream, ...)                       \
+  do {                                                                           \
+    cudaEvent_t _pa = nullptr;                                                   \
+    if (::god::g_prof_on.load(std::memory_order_relaxed)) ::god::prof_begin((stream), &_pa); \
+    kernel<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);                  \
+    ::god::g_launches.fetch_add(1, std::memory_order_relaxed);                   \
+    cudaError_t _le = cudaGetLastError();                                        \
+    if (_pa) ::god::prof_end(#kernel, (stream), _pa);                            \
+    if (_le != cudaSuccess) return ::god::cuda_fail(_le, #kernel, __FILE__, __LINE__); \
+  } while (0)
+
+int num_sms();
+
+// ------------------------------------------------------------------ memory
+// Stream-ordered device allocation (cudaMallocAsync on the device's default
+// pool, kept cached by a high release threshold).
+int dmalloc(void** p, size_t bytes, cudaStream_t st);
+void dfree(void* p, cudaStream_t st);
+
+template <typename T>
+struct DBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  cudaStream_t st = 0;
+  DBuf() = default;
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  ~DBuf() { release(); }
+  int alloc(size_t count, cudaStream_t s) {
+    release();
+    st = s;
+    n = count;
+    if (count == 0) count = 1;
+    return dmalloc((void**)&p, count * sizeof(T), s);
+  }
+  void release() {
+    if (p) dfree(p, st);
+    p = nullptr;
+    n = 0;
+  }
+  T* take() {
+    T* r = p;
+    p = nullptr;
+    n = 0;
+    return r;
+  }
+};
+
+bool is_device_ptr(const void* p);
+// Hands a malloc'ed host array to god_free's ownership registry.
+void register_host_array(void* p);
+
+// ------------------------------------------------------------------ pattern
+constexpr int kMaxPattern = 64;
+struct PatternInfo {
+  int p;                       // pattern length
+  int x;                       // weight (number of 1s)
+  int off[kMaxPattern];        // offsets of the 1s, ascending
+  int ones_prefix[kMaxPattern + 1];  // ones in P[0:i]
+};
+int parse_pattern(const char* s, PatternInfo* out);
+
+// Patterned length of a sequence of `len` bases under shift s (Sec. 3.2):
+// x * floor((len - s) / p) + ones(P[0 : (len - s) mod p]).
+__host__ __device__ inline uint64_t patterned_len(const PatternInfo& P, uint64_t len, uint32_t s) {
+  if (len <= s) return 0;
+  const uint64_t L = len - s;
+  return (uint64_t)P.x * (L / (uint64_t)P.p) + (uint64_t)P.ones_prefix[L % (uint64_t)P.p];
+}
+
+// ------------------------------------------------------------------ sketch
+// One patterned sequence of the virtual stream processed by the sketch kernel.
+struct SegDesc {
+  uint64_t byte_off;   // first byte of the source sequence in the byte buffer
+  uint32_t m;          // patterned bases of this segment (possibly a prefix)
+  uint32_t read;       // owning read (0 for the reference)
+  uint32_t shift;      // pattern shift s
+  uint32_t flags;      // kSegCapped when m is a prefix of the patterned read
+};
+constexpr uint32_t kSegCapped = 1u;
+
+// One minimizer: key = H(canonical k-mer); pos = original position of the
+// k-mer's first kept base; segz = (segment << 1) | z. 16 bytes.
+struct __align__(16) MinRec {
+  uint64_t key;
+  uint32_t pos;
+  uint32_t segz;
+};
+
+struct SketchTune {
+  int tile;     // owned k-mer positions per tile
+  int threads;  // threads per CTA
+};
+
+struct SketchJob {
+  const uint8_t* bytes;
+  const SegDesc* segs;
+  const uint64_t* seg_voff;   // n_seg + 1 virtual offsets (each segment m + 1)
+  uint32_t n_seg;
+  uint64_t V;                 // seg_voff[n_seg], read back by the caller
+  int k, w;
+  PatternInfo pat;
+  MinRec* out;
+  uint64_t out_cap;
+  uint32_t* seg_cnt;          // optional per-segment minimizer counts (zeroed by caller)
+  uint32_t* read_flag;        // optional: set to 1 for reads with an N in a capped segment
+};
+
+// Runs the fused sparsify + 2-bit code + hash + window-minimum + ordered
+// compaction kernel over the virtual stream. *total = minimizers found (they
+// were written only if total <= out_cap). Returns GOD_ETIMEOUT if a bounded
+// wait of the ordered compaction gave up.
+int run_sketch(const SketchJob& job, cudaStream_t st, uint64_t* total, const SketchTune* tune);
+SketchTune default_sketch_tune(int k, int w);
+
+// ------------------------------------------------------------------ scan
+// Exclusive prefix sum of n values into out (n + 1 entries: out[n] = total).
+int exclusive_scan_u32(const uint32_t* in, uint64_t* out, uint64_t n, cudaStream_t st);
+int exclusive_scan_u64(const uint64_t* in, uint64_t* out, uint64_t n, cudaStream_t st);
+
+// ------------------------------------------------------------------ radix sort
+// Stable LSD radix sort of (key, value) pairs by bits [0, key_bits) of the key.
+// keys/vals are sorted in place (alternate buffers are allocated internally).
+int radix_sort_pairs(uint64_t* keys, uint64_t* vals, uint64_t n, int key_bits, cudaStream_t st);
+
+// ------------------------------------------------------------------ index
+constexpr uint64_t kEmptyKey = ~0ULL;
+
+struct RmiLeaf {               // 16 bytes
+  uint64_t base_eps;           // base key (low 56 bits) | error bound (high 8 bits)
+  float slope;
+  float icept;
+};
+
+constexpr int kRootHidden = 32;
+struct RmiRoot {
+  float W1[kRootHidden];
+  float b1[kRootHidden];
+  float W2[kRootHidden];
+  float b2;
+  uint64_t kmin, kmax;
+  float inv_span;
+  uint32_t n_leaves;
+};
+
+struct DeviceIndex {           // what lookup kernels need, by value
+  const uint64_t* keys;        // n_keys ascending
+  const uint32_t* start;       // n_keys + 1
+  const uint64_t* ent;         // (pos << 1) | z
+  const ulonglong2* ht;        // {key, start | count << 32}
+  uint64_t ht_mask;
+  uint64_t n_keys;
+  const RmiLeaf* leaves;       // null without a learned index
+  const RmiRoot* root;         // device copy
+  uint32_t eps_max;
+};
+
+}  // namespace god
+
+struct god_index {
+  int device;
+  god::PatternInfo pat;
+  char pattern[god::kMaxPattern + 1];
+  int k, w;
+  uint32_t max_occ;
+  uint64_t ref_len;
+  uint64_t n_min;
+  uint64_t n_keys, n_ent;
+  uint64_t* d_keys;
+  uint32_t* d_start;
+  uint64_t* d_ent;
+  ulonglong2* d_ht;
+  uint64_t ht_cap;
+  god_params params;
+  // learned index
+  int has_rmi;
+  god::RmiRoot root;
+  god::RmiRoot* d_root;
+  god::RmiLeaf* d_leaves;
+  uint32_t rmi_fallback_leaves, rmi_max_eps;
+  double rmi_mean_eps, rmi_fallback_key_frac;
+  float rmi_loss;
+  uint64_t device_bytes;
+};
+
+namespace god {
+god::DeviceIndex device_view(const god_index* idx, int via);
+// Looks up n record keys: out[i] = start | count << 32 (0 when absent).
+int lookup_keys(const DeviceIndex& di, const uint64_t* keys, size_t key_stride_bytes, uint64_t n,
+                int via, uint64_t* out, cudaStream_t st);
+int build_index_device(god_index* idx, const uint8_t* d_ref, uint64_t len, cudaStream_t st);
+int build_rmi(god_index* idx, cudaStream_t st);
+int rmi_root_grad_device(const float* d_theta, int H, const float* d_x, const float* d_y, uint64_t n,
+                         float* d_grad, float* d_loss, cudaStream_t st);
+int seed_device(const god_index* idx, const uint8_t* d_reads, const uint64_t* d_offsets, uint32_t n,
+                uint64_t read_bytes, const god_seed_opts& o, cudaStream_t st, god_anchor** d_out,
+                uint64_t* n_anchors, god_anchor* user_out, uint64_t user_cap, bool user_out_device);
+}  // namespace god

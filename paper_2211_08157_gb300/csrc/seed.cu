@@ -1,0 +1,597 @@
+// Batched pattern alignment (Sec. 3.2) and compressed seeding (Sec. 3.3).
+//
+// All reads of a batch go through one pass of the sketch kernel as segments
+// (read, shift) of its virtual stream:
+//  * PA pass: every read at every shift s < p. With a limit t on the
+//    minimizers used per shift and odd k, only a prefix of t*w + w + k - 2
+//    patterned bases is sketched: windows starting before t*w are complete,
+//    disjoint windows [0, w), [w, 2w), ... each hold a minimizer, so an N-free
+//    prefix already contains the first t minimizers of the whole read. A read
+//    whose prefix holds an N is re-run at full length (fallback pass).
+//  * The read's alignment index a = the shift whose first t minimizers have the
+//    largest summed index count (smallest shift on ties, 0 when all are 0).
+//  * Seeding pass: the minimizers of the read at shift a. When the PA pass saw
+//    the whole read at shift a they are reused; otherwise the read is sketched
+//    again at shift a, full length.
+//  * Every seeding minimizer whose key is kept in the index yields one anchor
+//    per index entry; anchors are counted per read, offsets scanned, and each
+//    read's anchors are produced and sorted in on-chip memory in one step
+//    (a warp per read for short lists, a CTA per read with chunked bitonic
+//    sorts and merge-path passes for long ones).
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+
+namespace god {
+namespace {
+
+constexpr int kT = 256;
+constexpr uint32_t kSrcPA = 0, kSrcFB = 1, kSrcP2 = 2;
+constexpr int kSmallCap = 128;          // anchors per read for the warp path
+constexpr int kLargeThreads = 512;
+constexpr int kLargeCap = 8192;         // anchors sorted in shared memory at once
+
+inline unsigned grid_for(uint64_t n, int per = kT, unsigned cap_mult = 32) {
+  uint64_t b = (n + per - 1) / per;
+  b = std::max<uint64_t>(b, 1);
+  return (unsigned)std::min<uint64_t>(b, (uint64_t)num_sms() * cap_mult);
+}
+
+struct RecSet {
+  const MinRec* rec;
+  const uint64_t* sc;       // lookup result: start | count << 32
+  const uint64_t* seg_off;  // first record of each segment
+  const uint32_t* seg_cnt;  // records of each segment
+};
+struct RecSets {
+  RecSet s[3];
+};
+
+__global__ void make_pa_segments(const uint64_t* __restrict__ offs, uint32_t n, PatternInfo P, uint32_t cap,
+                                 SegDesc* __restrict__ segs, uint32_t* __restrict__ vlen, int* err) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t b = offs[i];
+    uint64_t e = offs[i + 1];
+    if (e < b || e - b >= (1ull << 31)) {
+      atomicExch(err, 1);
+      e = b;
+    }
+    const uint64_t len = e - b;
+    for (int s = 0; s < P.p; ++s) {
+      const uint64_t g = i * P.p + s;
+      const uint64_t m = patterned_len(P, len, s);
+      const uint32_t mm = (uint32_t)std::min<uint64_t>(m, cap);
+      segs[g] = SegDesc{b, mm, (uint32_t)i, (uint32_t)s, m > cap ? kSegCapped : 0u};
+      vlen[g] = mm + 1;
+    }
+  }
+}
+
+// Segments at full length for listed reads: all shifts (fallback PA) or the
+// chosen shift only (seeding pass).
+__global__ void make_list_segments(const uint64_t* __restrict__ offs, const uint32_t* __restrict__ list, uint32_t nl,
+                                   PatternInfo P, int all_shifts, const uint32_t* __restrict__ shift,
+                                   SegDesc* __restrict__ segs, uint32_t* __restrict__ vlen) {
+  for (uint64_t li = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; li < nl; li += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t i = list[li];
+    const uint64_t b = offs[i], len = offs[i + 1] - b;
+    if (all_shifts) {
+      for (int s = 0; s < P.p; ++s) {
+        const uint64_t m = patterned_len(P, len, s);
+        segs[li * P.p + s] = SegDesc{b, (uint32_t)m, i, (uint32_t)s, 0u};
+        vlen[li * P.p + s] = (uint32_t)m + 1;
+      }
+    } else {
+      const uint32_t s = shift[i];
+      const uint64_t m = patterned_len(P, len, s);
+      segs[li] = SegDesc{b, (uint32_t)m, i, s, 0u};
+      vlen[li] = (uint32_t)m + 1;
+    }
+  }
+}
+
+__device__ __forceinline__ uint64_t shift_sum(const RecSet& S, uint64_t g, uint32_t t) {
+  const uint64_t beg = S.seg_off[g];
+  const uint32_t c = S.seg_cnt[g];
+  const uint32_t use = t ? min(c, t) : c;
+  uint64_t sum = 0;
+  for (uint32_t j = 0; j < use; ++j) sum += S.sc[beg + j] >> 32;
+  return sum;
+}
+
+// Pattern alignment over the PA pass: one thread per read.
+__global__ void pa_select(uint32_t n, int p, uint32_t t, const SegDesc* __restrict__ segs, RecSet S,
+                          const uint32_t* __restrict__ need_full, uint32_t* __restrict__ shift,
+                          uint32_t* __restrict__ src, uint32_t* __restrict__ seed_seg, uint32_t* __restrict__ fb_flag,
+                          uint32_t* __restrict__ p2_flag) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    if (need_full[i]) {
+      fb_flag[i] = 1;
+      p2_flag[i] = 0;
+      src[i] = kSrcFB;
+      continue;
+    }
+    uint64_t best = 0;
+    uint32_t a = 0;
+    for (int s = 0; s < p; ++s) {
+      const uint64_t sum = shift_sum(S, i * p + s, t);
+      if (sum > best) { best = sum; a = (uint32_t)s; }
+    }
+    shift[i] = a;
+    const bool capped = segs[i * p + a].flags & kSegCapped;
+    src[i] = capped ? kSrcP2 : kSrcPA;
+    seed_seg[i] = (uint32_t)(i * p + a);
+    fb_flag[i] = 0;
+    p2_flag[i] = capped;
+  }
+}
+
+// Pattern alignment of fallback reads over their full-length segments.
+__global__ void pa_select_list(const uint32_t* __restrict__ list, uint32_t nl, int p, uint32_t t, RecSet S,
+                               uint32_t* __restrict__ shift, uint32_t* __restrict__ seed_seg) {
+  for (uint64_t li = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; li < nl; li += (uint64_t)gridDim.x * blockDim.x) {
+    uint64_t best = 0;
+    uint32_t a = 0;
+    for (int s = 0; s < p; ++s) {
+      const uint64_t sum = shift_sum(S, li * p + s, t);
+      if (sum > best) { best = sum; a = (uint32_t)s; }
+    }
+    const uint32_t i = list[li];
+    shift[i] = a;
+    seed_seg[i] = (uint32_t)(li * p + a);
+  }
+}
+
+__global__ void set_seed_seg_list(const uint32_t* __restrict__ list, uint32_t nl, uint32_t* __restrict__ seed_seg) {
+  for (uint64_t li = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; li < nl; li += (uint64_t)gridDim.x * blockDim.x)
+    seed_seg[list[li]] = (uint32_t)li;
+}
+
+// Anchors per read = sum of index counts of its seeding minimizers (warp per read).
+__global__ void count_anchors(uint32_t n, RecSets sets, const uint32_t* __restrict__ src,
+                              const uint32_t* __restrict__ seed_seg, uint64_t* __restrict__ read_cnt) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x / 32);
+  for (uint64_t i = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) / 32; i < n; i += warps) {
+    const RecSet& S = sets.s[src[i]];
+    const uint32_t g = seed_seg[i];
+    const uint64_t beg = S.seg_off[g];
+    const uint32_t c = S.seg_cnt[g];
+    uint64_t sum = 0;
+    for (uint32_t j = lane; j < c; j += 32) sum += S.sc[beg + j] >> 32;
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, d);
+    if (lane == 0) read_cnt[i] = sum;
+  }
+}
+
+__global__ void classify_reads(uint32_t n, const uint64_t* __restrict__ read_off, uint32_t* __restrict__ small,
+                               uint32_t* __restrict__ large) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t c = read_off[i + 1] - read_off[i];
+    small[i] = (c > 0 && c <= kSmallCap) ? 1u : 0u;
+    large[i] = c > kSmallCap ? 1u : 0u;
+  }
+}
+
+__global__ void scatter_list(const uint32_t* __restrict__ flag, const uint64_t* __restrict__ pos, uint64_t n,
+                             uint32_t* __restrict__ list) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+    if (flag[i]) list[pos[i]] = (uint32_t)i;
+}
+
+__device__ __forceinline__ uint64_t anchor_key(uint64_t entry, uint32_t read_pos, uint32_t z) {
+  return ((entry >> 1) << 32) | ((uint64_t)read_pos << 1) | ((entry & 1u) ^ z);
+}
+
+__device__ __forceinline__ void store_anchor(god_anchor* out, uint32_t read, uint64_t key) {
+  uint4 v;
+  v.x = read;
+  v.y = (uint32_t)(key >> 1) & 0x7FFFFFFFu;
+  v.z = (uint32_t)(key >> 32);
+  v.w = (uint32_t)(key & 1u);
+  *reinterpret_cast<uint4*>(out) = v;
+}
+
+// Short anchor lists: one warp per read builds the list in shared memory and
+// places every anchor at its rank (keys are distinct within a read).
+__global__ void __launch_bounds__(kT) fill_sort_small(RecSets sets, const uint32_t* __restrict__ src,
+                                                      const uint32_t* __restrict__ seed_seg,
+                                                      const uint64_t* __restrict__ read_off,
+                                                      const uint32_t* __restrict__ list, uint32_t nl,
+                                                      const uint64_t* __restrict__ ent, god_anchor* __restrict__ out) {
+  __shared__ uint64_t buf[kT / 32][kSmallCap];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint64_t* B = buf[wid];
+  const uint64_t warps = (uint64_t)gridDim.x * (kT / 32);
+  for (uint64_t li = (blockIdx.x * (uint64_t)kT + threadIdx.x) / 32; li < nl; li += warps) {
+    const uint32_t i = list[li];
+    const uint64_t off = read_off[i];
+    const uint32_t n = (uint32_t)(read_off[i + 1] - off);
+    const RecSet& S = sets.s[src[i]];
+    const uint32_t g = seed_seg[i];
+    const uint64_t beg = S.seg_off[g];
+    const uint32_t cnt = S.seg_cnt[g];
+    uint32_t base = 0;
+    for (uint32_t r0 = 0; r0 < cnt; r0 += 32) {
+      const uint32_t r = r0 + lane;
+      uint32_t c = 0, start = 0, pos = 0, z = 0;
+      if (r < cnt) {
+        const uint64_t sc = S.sc[beg + r];
+        c = (uint32_t)(sc >> 32);
+        start = (uint32_t)sc;
+        if (c) {
+          const MinRec m = S.rec[beg + r];
+          pos = m.pos;
+          z = m.segz & 1u;
+        }
+      }
+      uint32_t incl = c;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += y;
+      }
+      const uint32_t excl = base + incl - c;
+      for (uint32_t e = 0; e < c; ++e) B[excl + e] = anchor_key(__ldg(ent + start + e), pos, z);
+      base += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    __syncwarp();
+    for (uint32_t e = lane; e < n; e += 32) {
+      const uint64_t key = B[e];
+      uint32_t rank = 0;
+      for (uint32_t f = 0; f < n; ++f) rank += B[f] < key;
+      store_anchor(out + off + rank, i, key);
+    }
+    __syncwarp();
+  }
+}
+
+// ---- CTA helpers for long lists
+__device__ __forceinline__ uint32_t block_excl_scan_u32(uint32_t v, uint32_t* total, uint32_t* warp_buf) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nw = blockDim.x / 32;
+  uint32_t x = v;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+    if (lane >= d) x += y;
+  }
+  if (lane == 31) warp_buf[wid] = x;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t run = 0;
+    for (int w = 0; w < nw; ++w) { const uint32_t c = warp_buf[w]; warp_buf[w] = run; run += c; }
+    warp_buf[nw] = run;
+  }
+  __syncthreads();
+  const uint32_t r = warp_buf[wid] + x - v;
+  *total = warp_buf[nw];
+  __syncthreads();
+  return r;
+}
+
+// Writes anchor keys with list index in [lo, hi) to dst[idx - lo].
+__device__ void fill_range(const RecSet& S, uint64_t beg, uint32_t cnt, const uint64_t* __restrict__ ent, uint64_t lo,
+                           uint64_t hi, uint64_t* dst, uint32_t* warp_buf) {
+  uint64_t base = 0;
+  for (uint32_t r0 = 0; r0 < cnt; r0 += blockDim.x) {
+    const uint32_t r = r0 + threadIdx.x;
+    uint32_t c = 0, start = 0, pos = 0, z = 0;
+    if (r < cnt) {
+      const uint64_t sc = S.sc[beg + r];
+      c = (uint32_t)(sc >> 32);
+      start = (uint32_t)sc;
+    }
+    uint32_t tot;
+    const uint32_t ex = block_excl_scan_u32(c, &tot, warp_buf);
+    if (base + tot > lo && base < hi && c) {
+      const uint64_t a0 = base + ex;
+      const uint64_t e_lo = a0 < lo ? lo - a0 : 0;
+      const uint64_t e_hi = a0 + c > hi ? (hi > a0 ? hi - a0 : 0) : c;
+      if (e_lo < e_hi) {
+        const MinRec m = S.rec[beg + r];
+        pos = m.pos;
+        z = m.segz & 1u;
+        for (uint64_t e = e_lo; e < e_hi; ++e) dst[a0 + e - lo] = anchor_key(__ldg(ent + start + e), pos, z);
+      }
+    }
+    base += tot;
+    if (base >= hi) break;
+  }
+}
+
+__device__ void bitonic_sort_smem(uint64_t* s, uint32_t n_pad) {
+  for (uint32_t k = 2; k <= n_pad; k <<= 1) {
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      for (uint32_t i = threadIdx.x; i < n_pad; i += blockDim.x) {
+        const uint32_t ixj = i ^ j;
+        if (ixj > i) {
+          const uint64_t a = s[i], b = s[ixj];
+          const bool up = (i & k) == 0;
+          if ((a > b) == up) { s[i] = b; s[ixj] = a; }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// CTA merge of sorted a[0, na) and b[0, nb) into o (merge path per thread).
+__device__ void cta_merge(const uint64_t* a, uint64_t na, const uint64_t* b, uint64_t nb, uint64_t* o) {
+  constexpr int IPT = 8;
+  const uint64_t total = na + nb;
+  for (uint64_t d0 = (uint64_t)threadIdx.x * IPT; d0 < total; d0 += (uint64_t)blockDim.x * IPT) {
+    uint64_t lo = d0 > nb ? d0 - nb : 0, hi = d0 < na ? d0 : na;
+    while (lo < hi) {
+      const uint64_t mid = (lo + hi) >> 1;
+      if (a[mid] <= b[d0 - 1 - mid]) lo = mid + 1; else hi = mid;
+    }
+    uint64_t i = lo, j = d0 - lo;
+    for (int t = 0; t < IPT && d0 + t < total; ++t) {
+      if (j >= nb || (i < na && a[i] <= b[j])) o[d0 + t] = a[i++];
+      else o[d0 + t] = b[j++];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kLargeThreads) fill_sort_large(RecSets sets, const uint32_t* __restrict__ src,
+                                                                 const uint32_t* __restrict__ seed_seg,
+                                                                 const uint64_t* __restrict__ read_off,
+                                                                 const uint32_t* __restrict__ list, uint32_t nl,
+                                                                 const uint64_t* __restrict__ ent,
+                                                                 god_anchor* __restrict__ out, uint64_t* tmp) {
+  extern __shared__ __align__(16) uint64_t sk[];  // kLargeCap keys
+  __shared__ uint32_t warp_buf[kLargeThreads / 32 + 1];
+  for (uint32_t li = blockIdx.x; li < nl; li += gridDim.x) {
+    const uint32_t i = list[li];
+    const uint64_t off = read_off[i];
+    const uint64_t n = read_off[i + 1] - off;
+    const RecSet& S = sets.s[src[i]];
+    const uint32_t g = seed_seg[i];
+    const uint64_t beg = S.seg_off[g];
+    const uint32_t cnt = S.seg_cnt[g];
+    if (n <= kLargeCap) {
+      uint32_t n_pad = 1;
+      while (n_pad < n) n_pad <<= 1;
+      fill_range(S, beg, cnt, ent, 0, n, sk, warp_buf);
+      for (uint32_t q = (uint32_t)n + threadIdx.x; q < n_pad; q += blockDim.x) sk[q] = ~0ULL;
+      __syncthreads();
+      bitonic_sort_smem(sk, n_pad);
+      for (uint32_t q = threadIdx.x; q < n; q += blockDim.x) store_anchor(out + off + q, i, sk[q]);
+      __syncthreads();
+      continue;
+    }
+    // long list: sorted runs of kLargeCap in tmp, then merge passes (ping-pong)
+    uint64_t* t0 = tmp + 2 * off;
+    uint64_t* t1 = t0 + n;
+    for (uint64_t c0 = 0; c0 < n; c0 += kLargeCap) {
+      const uint64_t c1 = std::min<uint64_t>(n, c0 + kLargeCap);
+      const uint32_t m = (uint32_t)(c1 - c0);
+      uint32_t n_pad = 1;
+      while (n_pad < m) n_pad <<= 1;
+      fill_range(S, beg, cnt, ent, c0, c1, sk, warp_buf);
+      for (uint32_t q = m + threadIdx.x; q < n_pad; q += blockDim.x) sk[q] = ~0ULL;
+      __syncthreads();
+      bitonic_sort_smem(sk, n_pad);
+      for (uint32_t q = threadIdx.x; q < m; q += blockDim.x) t0[c0 + q] = sk[q];
+      __syncthreads();
+    }
+    uint64_t* a = t0;
+    uint64_t* b = t1;
+    for (uint64_t run = kLargeCap; run < n; run <<= 1) {
+      for (uint64_t j = 0; j < n; j += 2 * run) {
+        const uint64_t na = std::min<uint64_t>(run, n - j);
+        const uint64_t nb = j + run < n ? std::min<uint64_t>(run, n - j - run) : 0;
+        cta_merge(a + j, na, a + j + na, nb, b + j);
+      }
+      __syncthreads();
+      uint64_t* t = a; a = b; b = t;
+    }
+    for (uint64_t q = threadIdx.x; q < n; q += blockDim.x) store_anchor(out + off + q, i, a[q]);
+    __syncthreads();
+  }
+}
+
+// ---- host helpers
+int compact_flags(const uint32_t* flags, uint64_t n, DBuf<uint32_t>& list, uint64_t* count, cudaStream_t st) {
+  DBuf<uint64_t> pos;
+  GOD_TRY(pos.alloc(n + 1, st));
+  GOD_TRY(exclusive_scan_u32(flags, pos.p, n, st));
+  uint64_t c = 0;
+  GOD_CK(cudaMemcpyAsync(&c, pos.p + n, 8, cudaMemcpyDeviceToHost, st));
+  GOD_CK(cudaStreamSynchronize(st));
+  *count = c;
+  GOD_TRY(list.alloc(c, st));
+  if (c && n) GOD_LAUNCH(scatter_list, grid_for(n), kT, 0, st, flags, pos.p, n, list.p);
+  return GOD_OK;
+}
+
+// One record set: sketch + lookup + per-segment offsets.
+struct SetBufs {
+  DBuf<SegDesc> segs;
+  DBuf<uint32_t> vlen;
+  DBuf<uint64_t> voff;
+  DBuf<MinRec> rec;
+  DBuf<uint64_t> sc;
+  DBuf<uint32_t> seg_cnt;
+  DBuf<uint64_t> seg_off;
+  uint64_t n_seg = 0, n_rec = 0;
+  RecSet view() const { return RecSet{rec.p, sc.p, seg_off.p, seg_cnt.p}; }
+};
+
+int sketch_and_lookup(const god_index* idx, const uint8_t* d_reads, SetBufs& B, uint32_t* read_flag, int via,
+                      cudaStream_t st) {
+  GOD_TRY(B.voff.alloc(B.n_seg + 1, st));
+  GOD_TRY(exclusive_scan_u32(B.vlen.p, B.voff.p, B.n_seg, st));
+  uint64_t V = 0;
+  GOD_CK(cudaMemcpyAsync(&V, B.voff.p + B.n_seg, 8, cudaMemcpyDeviceToHost, st));
+  GOD_CK(cudaStreamSynchronize(st));
+  GOD_TRY(B.seg_cnt.alloc(B.n_seg, st));
+  SketchJob job{};
+  job.bytes = d_reads;
+  job.segs = B.segs.p;
+  job.seg_voff = B.voff.p;
+  job.n_seg = (uint32_t)B.n_seg;
+  job.V = V;
+  job.k = idx->k;
+  job.w = idx->w;
+  job.pat = idx->pat;
+  job.seg_cnt = B.seg_cnt.p;
+  job.read_flag = read_flag;
+  uint64_t cap = std::min<uint64_t>(V, (uint64_t)((double)V * 2.6 / (idx->w + 1)) + 4 * B.n_seg + 4096);
+  uint64_t total = 0;
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    GOD_TRY(B.rec.alloc(cap, st));
+    GOD_CK(cudaMemsetAsync(B.seg_cnt.p, 0, B.n_seg * sizeof(uint32_t), st));
+    job.out = B.rec.p;
+    job.out_cap = cap;
+    GOD_TRY(run_sketch(job, st, &total, nullptr));
+    if (total <= cap) break;
+    cap = total;
+  }
+  B.n_rec = total;
+  GOD_TRY(B.sc.alloc(total, st));
+  GOD_TRY(lookup_keys(device_view(idx, via), &B.rec.p->key, sizeof(MinRec), total, via, B.sc.p, st));
+  GOD_TRY(B.seg_off.alloc(B.n_seg + 1, st));
+  GOD_TRY(exclusive_scan_u32(B.seg_cnt.p, B.seg_off.p, B.n_seg, st));
+  return GOD_OK;
+}
+
+}  // namespace
+
+int seed_device(const god_index* idx, const uint8_t* d_reads, const uint64_t* d_offs, uint32_t n, uint64_t read_bytes,
+                const god_seed_opts& o, cudaStream_t st, god_anchor** d_out, uint64_t* n_anchors, god_anchor* user_out,
+                uint64_t user_cap, bool user_out_device) {
+  (void)read_bytes;
+  (void)user_out_device;
+  *n_anchors = 0;
+  if (n == 0) return GOD_OK;
+  const PatternInfo& P = idx->pat;
+  const int p = P.p;
+  const uint32_t t = (o.pa_t != UINT32_MAX) ? o.pa_t : idx->params.pa_t;
+  const int via = (o.via < 0) ? (idx->params.index_kind == GOD_INDEX_LEARNED && idx->has_rmi ? 1 : 0)
+                              : ((o.via == 1 && idx->has_rmi) ? 1 : 0);
+  const int k = idx->k, w = idx->w;
+  if ((uint64_t)n * p >= (1ull << 31)) {
+    set_error("seed: too many reads for this pattern length");
+    return GOD_EINVAL;
+  }
+  // prefix cap for pattern alignment (odd k only: even k admits palindromic
+  // windows without a minimizer, which would void the prefix guarantee)
+  uint32_t cap = 0xFFFFFFFEu;
+  if (t > 0 && (k & 1)) {
+    const uint64_t c = (uint64_t)t * w + w + k - 2;
+    if (c < cap) cap = (uint32_t)c;
+  }
+
+  DBuf<int> err;
+  GOD_TRY(err.alloc(1, st));
+  GOD_CK(cudaMemsetAsync(err.p, 0, sizeof(int), st));
+  DBuf<uint32_t> need_full, shift, src, seed_seg, fb_flag, p2_flag;
+  GOD_TRY(need_full.alloc(n, st));
+  GOD_TRY(shift.alloc(n, st));
+  GOD_TRY(src.alloc(n, st));
+  GOD_TRY(seed_seg.alloc(n, st));
+  GOD_TRY(fb_flag.alloc(n, st));
+  GOD_TRY(p2_flag.alloc(n, st));
+  GOD_CK(cudaMemsetAsync(need_full.p, 0, n * sizeof(uint32_t), st));
+
+  // ---- PA pass
+  SetBufs PA;
+  PA.n_seg = (uint64_t)n * p;
+  GOD_TRY(PA.segs.alloc(PA.n_seg, st));
+  GOD_TRY(PA.vlen.alloc(PA.n_seg, st));
+  GOD_LAUNCH(make_pa_segments, grid_for(n), kT, 0, st, d_offs, n, P, cap, PA.segs.p, PA.vlen.p, err.p);
+  int herr = 0;
+  GOD_CK(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  GOD_CK(cudaStreamSynchronize(st));
+  if (herr) {
+    set_error("seed: offsets must be non-decreasing and each read < 2^31 bytes");
+    return GOD_EINVAL;
+  }
+  GOD_TRY(sketch_and_lookup(idx, d_reads, PA, need_full.p, via, st));
+  GOD_LAUNCH(pa_select, grid_for(n), kT, 0, st, n, p, t, PA.segs.p, PA.view(), need_full.p, shift.p, src.p,
+             seed_seg.p, fb_flag.p, p2_flag.p);
+
+  // ---- fallback: full-length pattern alignment for reads with N in the prefix
+  SetBufs FB;
+  DBuf<uint32_t> fb_list;
+  uint64_t n_fb = 0;
+  GOD_TRY(compact_flags(fb_flag.p, n, fb_list, &n_fb, st));
+  if (n_fb) {
+    FB.n_seg = n_fb * p;
+    GOD_TRY(FB.segs.alloc(FB.n_seg, st));
+    GOD_TRY(FB.vlen.alloc(FB.n_seg, st));
+    GOD_LAUNCH(make_list_segments, grid_for(n_fb), kT, 0, st, d_offs, fb_list.p, (uint32_t)n_fb, P, 1, shift.p,
+               FB.segs.p, FB.vlen.p);
+    GOD_TRY(sketch_and_lookup(idx, d_reads, FB, nullptr, via, st));
+    GOD_LAUNCH(pa_select_list, grid_for(n_fb), kT, 0, st, fb_list.p, (uint32_t)n_fb, p, t, FB.view(), shift.p,
+               seed_seg.p);
+  }
+  // ---- seeding pass for reads whose shift-a segment was a prefix
+  SetBufs P2;
+  DBuf<uint32_t> p2_list;
+  uint64_t n_p2 = 0;
+  GOD_TRY(compact_flags(p2_flag.p, n, p2_list, &n_p2, st));
+  if (n_p2) {
+    P2.n_seg = n_p2;
+    GOD_TRY(P2.segs.alloc(P2.n_seg, st));
+    GOD_TRY(P2.vlen.alloc(P2.n_seg, st));
+    GOD_LAUNCH(make_list_segments, grid_for(n_p2), kT, 0, st, d_offs, p2_list.p, (uint32_t)n_p2, P, 0, shift.p,
+               P2.segs.p, P2.vlen.p);
+    GOD_TRY(sketch_and_lookup(idx, d_reads, P2, nullptr, via, st));
+    GOD_LAUNCH(set_seed_seg_list, grid_for(n_p2), kT, 0, st, p2_list.p, (uint32_t)n_p2, seed_seg.p);
+  }
+  if (o.shifts_out) {
+    GOD_CK(cudaMemcpyAsync(o.shifts_out, shift.p, n * sizeof(uint32_t), cudaMemcpyDefault, st));
+  }
+
+  // ---- anchors per read
+  RecSets sets;
+  sets.s[kSrcPA] = PA.view();
+  sets.s[kSrcFB] = FB.view();
+  sets.s[kSrcP2] = P2.view();
+  DBuf<uint64_t> read_cnt, read_off;
+  GOD_TRY(read_cnt.alloc(n, st));
+  GOD_TRY(read_off.alloc((uint64_t)n + 1, st));
+  GOD_LAUNCH(count_anchors, grid_for((uint64_t)n * 32), kT, 0, st, n, sets, src.p, seed_seg.p, read_cnt.p);
+  GOD_TRY(exclusive_scan_u64(read_cnt.p, read_off.p, n, st));
+  uint64_t total = 0;
+  GOD_CK(cudaMemcpyAsync(&total, read_off.p + n, 8, cudaMemcpyDeviceToHost, st));
+  GOD_CK(cudaStreamSynchronize(st));
+  *n_anchors = total;
+  god_anchor* out = user_out;
+  if (user_out) {
+    if (total > user_cap) return GOD_ERANGE;
+  } else {
+    GOD_TRY(dmalloc((void**)&out, std::max<uint64_t>(total, 1) * sizeof(god_anchor), st));
+    *d_out = out;
+  }
+  if (total == 0) return GOD_OK;
+
+  // ---- fill + sort per read
+  DBuf<uint32_t> fsmall, flarge, lsmall, llarge;
+  GOD_TRY(fsmall.alloc(n, st));
+  GOD_TRY(flarge.alloc(n, st));
+  GOD_LAUNCH(classify_reads, grid_for(n), kT, 0, st, n, read_off.p, fsmall.p, flarge.p);
+  uint64_t n_small = 0, n_large = 0;
+  GOD_TRY(compact_flags(fsmall.p, n, lsmall, &n_small, st));
+  GOD_TRY(compact_flags(flarge.p, n, llarge, &n_large, st));
+  if (n_small)
+    GOD_LAUNCH(fill_sort_small, grid_for(n_small * 32, kT, 64), kT, 0, st, sets, src.p, seed_seg.p, read_off.p,
+               lsmall.p, (uint32_t)n_small, idx->d_ent, out);
+  if (n_large) {
+    DBuf<uint64_t> tmp;
+    GOD_TRY(tmp.alloc(2 * total, st));  // indexed by the read's anchor offset
+    const size_t smem = kLargeCap * sizeof(uint64_t);
+    GOD_CK(cudaFuncSetAttribute(fill_sort_large, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const unsigned grid = (unsigned)std::min<uint64_t>(n_large, (uint64_t)num_sms() * 3);
+    GOD_LAUNCH(fill_sort_large, grid, kLargeThreads, smem, st, sets, src.p, seed_seg.p, read_off.p, llarge.p,
+               (uint32_t)n_large, idx->d_ent, out, tmp.p);
+  }
+  return GOD_OK;
+}
+
+}  // namespace god

@@ -1,0 +1,343 @@
+// Continuous-batching seeding server over one resident index.
+//
+// Requests (read batches) are queued on submit. Each of `slots` worker threads
+// owns a CUDA stream and pinned staging buffers; whenever it is free it admits
+// the oldest waiting request plus as many further waiting requests as fit in
+// max_batch_bases, provided the batch's device-memory estimate fits in what
+// the budget has left. The merged batch runs through the same batched seeding
+// pass as god_seed (one sketch launch over all of its reads), then the sorted
+// anchor list is cut back into per-request arrays by read range (anchors are
+// sorted by read, so each request owns one contiguous run). Slots run
+// concurrently, so requests that arrive while others are on the GPU overlap
+// with them. Integer results do not depend on how requests were merged.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "common.cuh"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+  uint64_t id;
+  std::vector<uint8_t> reads;
+  std::vector<uint64_t> offs;   // n + 1, rebased to 0
+  uint32_t n;
+  uint64_t bases;
+  Clock::time_point t_submit, t_done;
+  bool done = false;
+  bool merged = false;
+  int rc = GOD_OK;
+  god_anchor* result = nullptr;
+  uint64_t n_result = 0;
+};
+
+// Device bytes a batch may hold at its peak: input, segment tables, minimizer
+// records, lookups and the anchor output (estimated at 2 anchors per kept
+// minimizer), with a safety factor.
+uint64_t batch_bytes_estimate(const god_index* idx, uint64_t bases, uint64_t n) {
+  const double mins = (double)bases * idx->pat.x / idx->pat.p * 2.0 / (idx->w + 1) * idx->pat.p;
+  const double b = (double)bases * 1.0 + (double)n * (8 + 48.0 * idx->pat.p) + mins * (16 + 8 + 8) +
+                   mins * 2.0 * 16 * 2;
+  return (uint64_t)(b * 1.5) + (16ull << 20);
+}
+
+}  // namespace
+
+struct god_server {
+  const god_index* idx = nullptr;
+  god_server_config cfg{};
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<Request*> queue;
+  std::unordered_map<uint64_t, Request*> reqs;
+  std::vector<std::thread> workers;
+  uint64_t next_id = 1;
+  uint64_t mem_in_use = 0;
+  uint64_t inflight = 0;
+  bool stop = false;
+  god_server_stats st{};
+};
+
+namespace {
+
+void worker_main(god_server* S, int slot) {
+  cudaSetDevice(S->idx->device);
+  cudaStream_t stream;
+  cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking);
+  uint8_t* h_reads = nullptr;
+  uint64_t* h_offs = nullptr;
+  god_anchor* h_out = nullptr;
+  size_t cap_reads = 0, cap_offs = 0, cap_out = 0;
+  (void)slot;
+  while (true) {
+    std::vector<Request*> batch;
+    uint64_t est = 0;
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      while (true) {
+        if (S->stop) break;
+        if (!S->queue.empty()) {
+          // admission: oldest request first, then merge while it fits
+          uint64_t bases = 0, reads = 0;
+          size_t take = 0;
+          for (size_t i = 0; i < S->queue.size(); ++i) {
+            Request* r = S->queue[i];
+            if (take > 0 && bases + r->bases > S->cfg.max_batch_bases) break;
+            bases += r->bases;
+            reads += r->n;
+            ++take;
+          }
+          est = batch_bytes_estimate(S->idx, bases, reads);
+          // shrink the batch until it fits the remaining budget
+          while (take > 1 && S->mem_in_use + est > S->cfg.mem_budget) {
+            --take;
+            bases -= S->queue[take]->bases;
+            reads -= S->queue[take]->n;
+            est = batch_bytes_estimate(S->idx, bases, reads);
+          }
+          if (S->mem_in_use + est <= S->cfg.mem_budget) {
+            for (size_t i = 0; i < take; ++i) {
+              batch.push_back(S->queue.front());
+              S->queue.pop_front();
+            }
+            S->mem_in_use += est;
+            S->inflight++;
+            S->st.batches++;
+            S->st.max_inflight_batches = std::max(S->st.max_inflight_batches, S->inflight);
+            if (batch.size() > 1) S->st.merged_requests += batch.size();
+            break;
+          }
+          if (S->inflight == 0) {
+            // a single request larger than the whole budget: reject it
+            Request* r = S->queue.front();
+            S->queue.pop_front();
+            r->rc = GOD_ENOMEM;
+            r->done = true;
+            r->t_done = Clock::now();
+            S->st.rejected++;
+            S->st.completed++;
+            S->cv_done.notify_all();
+            continue;
+          }
+        }
+        S->cv_work.wait(lk);
+      }
+      if (S->stop && batch.empty()) break;
+    }
+    // ---- concatenate the batch into pinned staging
+    uint64_t bases = 0, n = 0;
+    for (Request* r : batch) { bases += r->bases; n += r->n; }
+    int rc = GOD_OK;
+    if (bases > cap_reads) {
+      if (h_reads) cudaFreeHost(h_reads);
+      cap_reads = std::max<uint64_t>(bases, 1 << 20);
+      if (cudaMallocHost(&h_reads, cap_reads) != cudaSuccess) { h_reads = nullptr; cap_reads = 0; rc = GOD_ENOMEM; }
+    }
+    if (rc == GOD_OK && n + 1 > cap_offs) {
+      if (h_offs) cudaFreeHost(h_offs);
+      cap_offs = std::max<uint64_t>(n + 1, 1 << 16);
+      if (cudaMallocHost(&h_offs, cap_offs * 8) != cudaSuccess) { h_offs = nullptr; cap_offs = 0; rc = GOD_ENOMEM; }
+    }
+    std::vector<uint64_t> first_read;
+    if (rc == GOD_OK) {
+      uint64_t bo = 0, ro = 0;
+      for (Request* r : batch) {
+        memcpy(h_reads + bo, r->reads.data(), r->bases);
+        for (uint32_t i = 0; i < r->n; ++i) h_offs[ro + i] = bo + r->offs[i];
+        first_read.push_back(ro);
+        bo += r->bases;
+        ro += r->n;
+      }
+      h_offs[ro] = bo;
+    }
+    // ---- device pass
+    god::DBuf<uint8_t> d_reads;
+    god::DBuf<uint64_t> d_offs;
+    god_anchor* d_out = nullptr;
+    uint64_t total = 0;
+    if (rc == GOD_OK) rc = d_reads.alloc(bases, stream);
+    if (rc == GOD_OK) rc = d_offs.alloc(n + 1, stream);
+    if (rc == GOD_OK && bases) rc = cudaMemcpyAsync(d_reads.p, h_reads, bases, cudaMemcpyHostToDevice, stream) ? GOD_ECUDA : GOD_OK;
+    if (rc == GOD_OK) rc = cudaMemcpyAsync(d_offs.p, h_offs, (n + 1) * 8, cudaMemcpyHostToDevice, stream) ? GOD_ECUDA : GOD_OK;
+    if (rc == GOD_OK) {
+      god_seed_opts o;
+      god_seed_opts_init(&o);
+      o.stream = stream;
+      rc = god::seed_device(S->idx, d_reads.p, d_offs.p, (uint32_t)n, bases, o, stream, &d_out, &total, nullptr, 0,
+                            true);
+    }
+    if (rc == GOD_OK && total > cap_out) {
+      if (h_out) cudaFreeHost(h_out);
+      cap_out = std::max<uint64_t>(total, 1 << 16);
+      if (cudaMallocHost(&h_out, cap_out * sizeof(god_anchor)) != cudaSuccess) { h_out = nullptr; cap_out = 0; rc = GOD_ENOMEM; }
+    }
+    if (rc == GOD_OK && total)
+      rc = cudaMemcpyAsync(h_out, d_out, total * sizeof(god_anchor), cudaMemcpyDeviceToHost, stream) ? GOD_ECUDA : GOD_OK;
+    if (d_out) god::dfree(d_out, stream);
+    d_reads.release();
+    d_offs.release();
+    if (cudaStreamSynchronize(stream) != cudaSuccess && rc == GOD_OK) rc = GOD_ECUDA;
+    // ---- split per request
+    for (size_t bi = 0; bi < batch.size(); ++bi) {
+      Request* r = batch[bi];
+      r->rc = rc;
+      if (rc == GOD_OK) {
+        const uint32_t lo = (uint32_t)first_read[bi], hi = lo + r->n;
+        const god_anchor* b = std::lower_bound(h_out, h_out + total, lo,
+                                               [](const god_anchor& a, uint32_t v) { return a.read_id < v; });
+        const god_anchor* e = std::lower_bound(b, (const god_anchor*)h_out + total, hi,
+                                               [](const god_anchor& a, uint32_t v) { return a.read_id < v; });
+        r->n_result = (uint64_t)(e - b);
+        r->result = (god_anchor*)malloc(std::max<uint64_t>(r->n_result, 1) * sizeof(god_anchor));
+        if (!r->result) r->rc = GOD_ENOMEM;
+        else
+          for (uint64_t i = 0; i < r->n_result; ++i) {
+            r->result[i] = b[i];
+            r->result[i].read_id -= lo;
+          }
+      }
+      r->merged = batch.size() > 1;
+      std::vector<uint8_t>().swap(r->reads);
+    }
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      const auto now = Clock::now();
+      for (Request* r : batch) {
+        r->done = true;
+        r->t_done = now;
+        S->st.completed++;
+      }
+      S->mem_in_use -= est;
+      S->inflight--;
+    }
+    S->cv_done.notify_all();
+    S->cv_work.notify_all();
+  }
+  if (h_reads) cudaFreeHost(h_reads);
+  if (h_offs) cudaFreeHost(h_offs);
+  if (h_out) cudaFreeHost(h_out);
+  cudaStreamDestroy(stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+void god_server_config_init(god_server_config* c) {
+  if (!c) return;
+  c->slots = 4;
+  c->mem_budget = 0;
+  c->max_batch_bases = 64ull << 20;
+}
+
+int god_server_create(const god_index* idx, const god_server_config* cfg, god_server** out) {
+  if (!idx || !out) return GOD_EINVAL;
+  god_server* S = new god_server();
+  S->idx = idx;
+  god_server_config_init(&S->cfg);
+  if (cfg) S->cfg = *cfg;
+  if (S->cfg.slots < 1) S->cfg.slots = 1;
+  if (S->cfg.slots > 32) S->cfg.slots = 32;
+  if (S->cfg.max_batch_bases == 0) S->cfg.max_batch_bases = 64ull << 20;
+  if (S->cfg.mem_budget == 0) {
+    size_t fr = 0, tot = 0;
+    cudaSetDevice(idx->device);
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+      delete S;
+      return god::cuda_fail(cudaGetLastError(), "cudaMemGetInfo", __FILE__, __LINE__);
+    }
+    S->cfg.mem_budget = (uint64_t)(fr * 0.8);
+  }
+  for (int i = 0; i < S->cfg.slots; ++i) S->workers.emplace_back(worker_main, S, i);
+  *out = S;
+  return GOD_OK;
+}
+
+int god_server_submit(god_server* S, const uint8_t* reads, const uint64_t* offsets, uint32_t n, uint64_t* request_id) {
+  if (!S || !request_id || (n && (!reads || !offsets))) return GOD_EINVAL;
+  Request* r = new Request();
+  r->n = n;
+  const uint64_t b0 = n ? offsets[0] : 0;
+  r->offs.resize((size_t)n + 1);
+  for (uint32_t i = 0; i <= n; ++i) {
+    if (i && (offsets[i] < offsets[i - 1] || offsets[i] - offsets[i - 1] >= (1ull << 31))) {
+      delete r;
+      god::set_error("offsets must be non-decreasing and each read < 2^31 bytes");
+      return GOD_EINVAL;
+    }
+    r->offs[i] = offsets[i] - b0;
+  }
+  r->bases = n ? offsets[n] - b0 : 0;
+  r->reads.assign(reads + b0, reads + b0 + r->bases);
+  r->t_submit = Clock::now();
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    r->id = S->next_id++;
+    S->reqs[r->id] = r;
+    S->queue.push_back(r);
+    S->st.submitted++;
+  }
+  S->cv_work.notify_one();
+  *request_id = r->id;
+  return GOD_OK;
+}
+
+int god_server_wait(god_server* S, uint64_t id, int timeout_ms, god_anchor** anchors, uint64_t* n_anchors,
+                    double* latency_s) {
+  if (!S || !anchors || !n_anchors) return GOD_EINVAL;
+  std::unique_lock<std::mutex> lk(S->mu);
+  auto it = S->reqs.find(id);
+  if (it == S->reqs.end()) return GOD_EINVAL;
+  Request* r = it->second;
+  if (timeout_ms < 0) S->cv_done.wait(lk, [&] { return r->done; });
+  else if (!S->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), [&] { return r->done; })) return GOD_EBUSY;
+  S->reqs.erase(it);
+  lk.unlock();
+  const int rc = r->rc;
+  if (latency_s) *latency_s = std::chrono::duration<double>(r->t_done - r->t_submit).count();
+  *anchors = nullptr;
+  *n_anchors = 0;
+  if (rc == GOD_OK) {
+    *anchors = r->result;
+    *n_anchors = r->n_result;
+    god::register_host_array(r->result);
+  } else if (r->result) {
+    free(r->result);
+  }
+  delete r;
+  return rc;
+}
+
+int god_server_get_stats(god_server* S, god_server_stats* st) {
+  if (!S || !st) return GOD_EINVAL;
+  std::lock_guard<std::mutex> lk(S->mu);
+  *st = S->st;
+  return GOD_OK;
+}
+
+int god_server_destroy(god_server* S) {
+  if (!S) return GOD_EINVAL;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->stop = true;
+  }
+  S->cv_work.notify_all();
+  for (auto& t : S->workers) t.join();
+  for (auto& kv : S->reqs) {
+    if (kv.second->result) free(kv.second->result);
+    delete kv.second;
+  }
+  delete S;
+  return GOD_OK;
+}
+
+}  // extern "C"
