@@ -183,6 +183,41 @@ int god_seed_device(const god_index *idx, const uint8_t *d_reads, const uint64_t
 int god_sketch(const uint8_t *seq, uint64_t len, const char *pattern, uint32_t shift, int k, int w,
                uint64_t *keys, uint32_t *pos, uint8_t *z, uint64_t cap, uint64_t *n_out, void *stream);
 
+/* ----------------------------------------------------------------- allocation-free sketch
+ * The paper has no counterpart to this entry point; it exists for callers that
+ * may not allocate device memory during a call (a host framework whose own
+ * allocator owns the device, a latency-critical loop that cannot afford the
+ * implicit synchronisation of cudaMalloc/cudaFree, a deployment that forbids
+ * allocation after start-up). It returns the same minimizers as god_sketch
+ * but calls no cudaMalloc, cudaFree or allocating library routine: the sketch
+ * kernel's scratch (ordered-compaction status words, tile ticket, counters,
+ * segment descriptor) lives in one 256 KiB device array that every GPU loading
+ * the library holds until the process exits.
+ *   d_seq    device memory, len bytes (host pointers are rejected: copying
+ *            them would need a device buffer).
+ *   d_out    device memory for cap records {key, pos, z} (16 bytes each), in
+ *            ascending patterned position.
+ *   *n_out   the number of minimizers; when it exceeds cap, only the first cap
+ *            records are written and GOD_ERANGE is returned.
+ * Sequences whose patterned length (under pattern and shift) exceeds
+ * GOD_NOALLOC_MAX_PATTERNED are rejected with GOD_EINVAL before any work.
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture. All calls on a device share the array and each
+ * call clears what it needs at its start, so calls that overlap on the GPU
+ * (e.g. on two streams) race: serialise them. The stream is synchronised
+ * before the call returns. */
+typedef struct {
+  uint64_t key;
+  uint32_t pos;
+  uint32_t z;
+} god_minimizer;
+
+#define GOD_NOALLOC_MAX_PATTERNED 67084287ULL
+
+int god_sketch_noalloc(const uint8_t *d_seq, uint64_t len, const char *pattern, uint32_t shift, int k,
+                       int w, god_minimizer *d_out, uint64_t cap, uint64_t *n_out, void *stream);
+
 /* ----------------------------------------------------------------- learned index
  * Gradient of the root MLP's mean squared error (1 -> H -> 1, ReLU; parameter
  * layout W1[H], b1[H], W2[H], b2) over samples (x[i], y[i]), computed by the

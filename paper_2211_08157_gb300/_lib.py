@@ -121,6 +121,7 @@ SIGNATURES = {
     "god_seed_into": (I32, [P_, P_, P_, U32, P_, U64, C.POINTER(U64), C.POINTER(SeedOpts)]),
     "god_seed_device": (I32, [P_, P_, P_, U32, C.POINTER(P_), C.POINTER(U64), C.POINTER(SeedOpts)]),
     "god_sketch": (I32, [P_, U64, C.c_char_p, U32, I32, I32, P_, P_, P_, U64, C.POINTER(U64), P_]),
+    "god_sketch_noalloc": (I32, [P_, U64, C.c_char_p, U32, I32, I32, P_, U64, C.POINTER(U64), P_]),
     "god_rmi_root_grad": (I32, [P_, I32, P_, P_, U64, P_, P_]),
     "god_free": (None, [P_]),
     "god_launch_count": (U64, []),

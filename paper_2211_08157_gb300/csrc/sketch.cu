@@ -27,6 +27,7 @@
 //  5. ordered compaction with a decoupled look-back over tile tickets, so the
 //     output is in stream order (segment, position) with no second pass.
 #include <algorithm>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -386,3 +387,126 @@ int run_sketch(const SketchJob& job, cudaStream_t st, uint64_t* total, const Ske
 }
 
 }  // namespace god
+
+// ------------------------------------------------------------------------
+// Allocation-free sketch entry point (god_sketch_noalloc). Some callers may
+// not allocate device memory at all during a call: a host framework whose own
+// allocator owns the whole device, a latency-critical loop that cannot take
+// the implicit synchronisation of cudaMalloc/cudaFree, or a deployment that
+// forbids allocation after start-up. For them the sketch kernel above runs
+// with its scratch (look-back status words, tile ticket, total, error flag,
+// the one segment descriptor) in a file-scope device array instead of a
+// stream-ordered allocation. The array is shared by every call on a device
+// and keeps the last call's contents; every word the kernel needs zeroed is
+// cleared by a small prep kernel at the start of each call, so calls that
+// overlap on the GPU (concurrent streams) race and must be serialised by the
+// caller.
+namespace god {
+namespace {
+
+constexpr uint64_t kNoAllocWords = 32768;                 // 256 KiB of scratch per device
+constexpr uint64_t kNoAllocTail = 8;                      // segment descriptor + offsets
+constexpr uint64_t kNoAllocMaxTiles = kNoAllocWords - kNoAllocTail - 4;
+static __device__ __align__(256) unsigned long long g_noalloc_scratch[kNoAllocWords];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+unsigned long long* g_noalloc_addr[kMaxDevices];          // device address of the array, per device
+
+__global__ void noalloc_prep(unsigned long long* scratch, uint64_t n_tiles, SegDesc seg, uint64_t V) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n_tiles + 4;
+       i += (uint64_t)gridDim.x * blockDim.x)
+    scratch[i] = 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *reinterpret_cast<SegDesc*>(scratch + kNoAllocWords - kNoAllocTail) = seg;
+    scratch[kNoAllocWords - 2] = 0;   // segment offsets {0, V}
+    scratch[kNoAllocWords - 1] = V;
+  }
+}
+
+// Device address of the scratch array on the current device, looked up once
+// per device (with that device current) and cached.
+int noalloc_scratch(unsigned long long** out) {
+  int dev = 0;
+  GOD_CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) {
+    set_error("device ordinal out of range");
+    return GOD_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)", __FILE__, __LINE__);
+    g_noalloc_addr[dev] = static_cast<unsigned long long*>(p);
+  }
+  *out = g_noalloc_addr[dev];
+  return GOD_OK;
+}
+
+}  // namespace
+}  // namespace god
+
+extern "C" int god_sketch_noalloc(const uint8_t* d_seq, uint64_t len, const char* pattern, uint32_t shift, int k,
+                                  int w, god_minimizer* d_out, uint64_t cap, uint64_t* n_out, void* stream) {
+  using namespace god;
+  if (!n_out) return GOD_EINVAL;
+  *n_out = 0;
+  PatternInfo P;
+  if (parse_pattern(pattern, &P) != GOD_OK || k < 1 || k > 28 || w < 1 || w > 255) {
+    set_error("god_sketch_noalloc: bad pattern, k or w");
+    return GOD_EINVAL;
+  }
+  if (len >= (1ULL << 32)) {
+    set_error("god_sketch_noalloc: sequence must be shorter than 2^32 bases");
+    return GOD_EINVAL;
+  }
+  const SketchTune tn{2048, 256};
+  const uint64_t m = patterned_len(P, len, shift);
+  const uint64_t V = m + 1;
+  const uint64_t n_tiles = (V + tn.tile - 1) / tn.tile;
+  if (n_tiles > kNoAllocMaxTiles) {
+    set_error("god_sketch_noalloc: patterned length exceeds GOD_NOALLOC_MAX_PATTERNED");
+    return GOD_EINVAL;
+  }
+  if ((len && !is_device_ptr(d_seq)) || (cap && !is_device_ptr(d_out))) {
+    set_error("god_sketch_noalloc: sequence and output must be device memory");
+    return GOD_EINVAL;
+  }
+  unsigned long long* scratch = nullptr;
+  GOD_TRY(noalloc_scratch(&scratch));
+  cudaStream_t st = (cudaStream_t)stream;
+  const SegDesc seg{0, (uint32_t)m, 0, shift, 0};
+  GOD_LAUNCH(noalloc_prep, (unsigned)std::min<uint64_t>((n_tiles + 4 + 255) / 256, 1024), 256, 0, st, scratch,
+             n_tiles, seg, V);
+  SketchArgs a;
+  a.job = SketchJob{};
+  a.job.bytes = d_seq;
+  a.job.segs = reinterpret_cast<const SegDesc*>(scratch + kNoAllocWords - kNoAllocTail);
+  a.job.seg_voff = reinterpret_cast<const uint64_t*>(scratch + kNoAllocWords - 2);
+  a.job.n_seg = 1;
+  a.job.V = V;
+  a.job.k = k;
+  a.job.w = w;
+  a.job.pat = P;
+  a.job.out = reinterpret_cast<MinRec*>(d_out);   // same 16-byte layout; segment 0 leaves z alone
+  a.job.out_cap = cap;
+  a.tile_status = scratch;
+  a.ticket = reinterpret_cast<unsigned int*>(scratch + n_tiles);
+  a.total = scratch + n_tiles + 1;
+  a.err = reinterpret_cast<int*>(scratch + n_tiles + 2);
+  a.n_tiles = n_tiles;
+  a.T = tn.tile;
+  const size_t smem = sketch_smem_bytes(tn.tile, k, w);
+  const int lrc = (k > 16) ? launch_sketch_t<256, true>(a, smem, st) : launch_sketch_t<256, false>(a, smem, st);
+  if (lrc != GOD_OK) return lrc;
+  unsigned long long host[2] = {0, 0};
+  GOD_CK(cudaMemcpyAsync(host, scratch + n_tiles + 1, sizeof host, cudaMemcpyDeviceToHost, st));
+  GOD_CK(cudaStreamSynchronize(st));
+  *n_out = host[0];
+  if ((int)(host[1] & 0xFFFFFFFFu) == GOD_ETIMEOUT) {
+    set_error("god_sketch_noalloc: ordered-compaction look-back wait gave up");
+    return GOD_ETIMEOUT;
+  }
+  return host[0] > cap ? GOD_ERANGE : GOD_OK;
+}
