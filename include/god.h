@@ -191,7 +191,7 @@ int god_sketch(const uint8_t *seq, uint64_t len, const char *pattern, uint32_t s
  * allocation after start-up). It returns the same minimizers as god_sketch
  * but calls no cudaMalloc, cudaFree or allocating library routine: the sketch
  * kernel's scratch (ordered-compaction status words, tile ticket, counters,
- * segment descriptor) lives in one 256 KiB device array that every GPU loading
+ * segment descriptor) lives in one 2 MiB device array that every GPU loading
  * the library holds until the process exits.
  *   d_seq    device memory, len bytes (host pointers are rejected: copying
  *            them would need a device buffer).
@@ -213,7 +213,7 @@ typedef struct {
   uint32_t z;
 } god_minimizer;
 
-#define GOD_NOALLOC_MAX_PATTERNED 67084287ULL
+#define GOD_NOALLOC_MAX_PATTERNED 45395007ULL
 
 int god_sketch_noalloc(const uint8_t *d_seq, uint64_t len, const char *pattern, uint32_t shift, int k,
                        int w, god_minimizer *d_out, uint64_t cap, uint64_t *n_out, void *stream);

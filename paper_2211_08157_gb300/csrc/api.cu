@@ -455,17 +455,9 @@ int god_sketch(const uint8_t* seq, uint64_t len, const char* pattern, uint32_t s
   job.k = k;
   job.w = w;
   job.pat = P;
-  uint64_t ocap = std::min<uint64_t>(m + 1, (uint64_t)((double)m * 2.6 / (w + 1)) + 4096);
   DBuf<MinRec> rec;
   uint64_t total = 0;
-  for (int attempt = 0; attempt < 2; ++attempt) {
-    GOD_TRY(rec.alloc(ocap, st));
-    job.out = rec.p;
-    job.out_cap = ocap;
-    GOD_TRY(run_sketch(job, st, &total, nullptr));
-    if (total <= ocap) break;
-    ocap = total;
-  }
+  GOD_TRY(run_sketch(job, st, rec, &total, nullptr));
   *n_out = total;
   if (total > cap) return GOD_ERANGE;
   if (total == 0) return GOD_OK;

@@ -145,11 +145,11 @@ struct SketchJob {
   uint32_t* read_flag;        // optional: set to 1 for reads with an N in a capped segment
 };
 
-// Runs the fused sparsify + 2-bit code + hash + window-minimum + ordered
-// compaction kernel over the virtual stream. *total = minimizers found (they
-// were written only if total <= out_cap). Returns GOD_ETIMEOUT if a bounded
-// wait of the ordered compaction gave up.
-int run_sketch(const SketchJob& job, cudaStream_t st, uint64_t* total, const SketchTune* tune);
+// Runs the fused sparsify + 2-bit code + hash + window-minimum kernel over the
+// virtual stream and returns its minimizer records in stream order (segment,
+// position) in `out`, allocated to exactly *total records. job.out / out_cap
+// are not used.
+int run_sketch(const SketchJob& job, cudaStream_t st, DBuf<MinRec>& out, uint64_t* total, const SketchTune* tune);
 SketchTune default_sketch_tune(int k, int w);
 
 // ------------------------------------------------------------------ scan

@@ -195,17 +195,9 @@ int build_index_device(god_index* idx, const uint8_t* d_ref, uint64_t len, cudaS
   job.k = idx->k;
   job.w = idx->w;
   job.pat = P;
-  uint64_t cap = std::min<uint64_t>(m + 1, (uint64_t)((double)m * 2.6 / (idx->w + 1)) + 4096);
   DBuf<MinRec> rec;
   uint64_t total = 0;
-  for (int attempt = 0; attempt < 2; ++attempt) {
-    GOD_TRY(rec.alloc(cap, st));
-    job.out = rec.p;
-    job.out_cap = cap;
-    GOD_TRY(run_sketch(job, st, &total, nullptr));
-    if (total <= cap) break;
-    cap = total;
-  }
+  GOD_TRY(run_sketch(job, st, rec, &total, nullptr));
   const uint64_t n = total;
   idx->n_min = n;
 

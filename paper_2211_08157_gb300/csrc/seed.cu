@@ -440,17 +440,9 @@ int sketch_and_lookup(const god_index* idx, const uint8_t* d_reads, SetBufs& B, 
   job.pat = idx->pat;
   job.seg_cnt = B.seg_cnt.p;
   job.read_flag = read_flag;
-  uint64_t cap = std::min<uint64_t>(V, (uint64_t)((double)V * 2.6 / (idx->w + 1)) + 4 * B.n_seg + 4096);
   uint64_t total = 0;
-  for (int attempt = 0; attempt < 2; ++attempt) {
-    GOD_TRY(B.rec.alloc(cap, st));
-    GOD_CK(cudaMemsetAsync(B.seg_cnt.p, 0, B.n_seg * sizeof(uint32_t), st));
-    job.out = B.rec.p;
-    job.out_cap = cap;
-    GOD_TRY(run_sketch(job, st, &total, nullptr));
-    if (total <= cap) break;
-    cap = total;
-  }
+  GOD_CK(cudaMemsetAsync(B.seg_cnt.p, 0, B.n_seg * sizeof(uint32_t), st));
+  GOD_TRY(run_sketch(job, st, B.rec, &total, nullptr));
   B.n_rec = total;
   GOD_TRY(B.sc.alloc(total, st));
   GOD_TRY(lookup_keys(device_view(idx, via), &B.rec.p->key, sizeof(MinRec), total, via, B.sc.p, st));

@@ -84,6 +84,9 @@ __device__ __forceinline__ void st_release_u64(unsigned long long* p, uint64_t v
 
 struct SketchArgs {
   SketchJob job;
+  uint32_t* tile_seg;          // first segment of each CTA tile
+  MinRec* staging;             // staged output: WT slots per warp sub-tile
+  uint32_t* sub_cnt;           // staged output: records of each sub-tile
   unsigned long long* tile_status;
   unsigned int* ticket;
   unsigned long long* total;
@@ -102,287 +105,518 @@ __device__ uint32_t find_segment(const uint64_t* voff, uint32_t n_seg, uint64_t 
   return lo;
 }
 
-template <int BLOCK, bool WIDE>
-__global__ void __launch_bounds__(BLOCK) sketch_kernel(SketchArgs a) {
+// Key storage: 32-bit when 2k <= 30 (key + 1 and the palindrome mark fit),
+// 64-bit otherwise. Hash arithmetic: 32-bit when 2k <= 32.
+template <typename KT>
+__device__ __forceinline__ KT palin_mark() { return (KT)~(KT)0; }
+
+constexpr int kBndCache = 256;  // segment boundaries cached per tile
+
+// Owned positions per warp sub-tile: as many as let one 8-base chunk per
+// thread cover the CTA tile plus its halo (multiple of 8, at least 64).
+__host__ __device__ inline int sub_tile_for(int warps, int k, int w) {
+  int wt = (8 * 32 * warps - 2 * (w - 1) - (k - 1)) / warps;
+  wt &= ~7;
+  return wt < 64 ? 64 : wt;
+}
+
+// Shared-memory layout of one CTA tile of T = WARPS * WT owned positions
+// (host and device agree on it).
+struct TileLayout {
+  int n_keys, n_codes, n_groups, n_chunks, n_win_w;
+  size_t off_sm, off_f, off_c, off_cst, off_nm, off_zb, off_sel, off_list, bytes;
+};
+
+__host__ __device__ inline TileLayout tile_layout(int warps, int WT, int k, int w, int kt) {
+  TileLayout L;
+  const int T = warps * WT;
+  L.n_keys = T + 2 * (w - 1);            // k-mer positions [A - w + 1, A + T + w - 1)
+  L.n_codes = L.n_keys + k - 1;          // bases of those k-mers
+  L.n_groups = (L.n_codes + 31) / 32;    // 32-base groups (packed words)
+  L.n_chunks = L.n_groups * 4;           // 8-base chunks
+  L.n_win_w = WT + w - 1;                // windows a warp evaluates
+  const int n_keys_w = WT + 2 * (w - 1);
+  size_t o = ((size_t)L.n_keys * kt + 15) & ~(size_t)15;        // K (whole tile)
+  L.off_sm = o;
+  o += (((size_t)2 * n_keys_w * kt) * warps + 15) & ~(size_t)15;  // per warp: S/M, SX
+  L.off_f = o;
+  o += (size_t)(L.n_groups + 1) * 8;
+  L.off_c = o;
+  o += (size_t)(L.n_groups + 1) * 8;
+  L.off_cst = o;
+  o += (size_t)L.n_chunks * 8;
+  L.off_nm = o;
+  o += (size_t)(L.n_groups + 1) * 4;
+  L.off_zb = o;
+  o += (size_t)L.n_keys;
+  L.off_sel = o;
+  o += (size_t)T;                        // selection flags
+  o = (o + 3) & ~(size_t)3;
+  L.off_list = o;
+  o += (size_t)T * 2;                    // per warp: selected positions (u16)
+  L.bytes = (o + 15) & ~(size_t)15;
+  return L;
+}
+
+__device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
+#pragma unroll
+  for (int d = 16; d >= 1; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+  return v;
+}
+
+// 64 bits of a big-endian bit stream {hi64, lo64} starting at bit s (0..63).
+__device__ __forceinline__ uint64_t take64_be(uint64_t w0, uint64_t w1, uint32_t s) {
+  const uint32_t a = (uint32_t)(w0 >> 32), b = (uint32_t)w0, c = (uint32_t)(w1 >> 32), d = (uint32_t)w1;
+  const uint32_t t = s & 31;
+  const bool hiw = s >= 32;
+  const uint32_t x0 = hiw ? b : a, x1 = hiw ? c : b, x2 = hiw ? d : c;
+  const uint32_t hi = __funnelshift_l(x1, x0, t);   // (x0:x1) << t, high word
+  const uint32_t lo = __funnelshift_l(x2, x1, t);
+  return ((uint64_t)hi << 32) | lo;
+}
+
+// 64 bits of a little-endian bit stream {lo64 = w0, hi64 = w1} starting at bit s.
+__device__ __forceinline__ uint64_t take64_le(uint64_t w0, uint64_t w1, uint32_t s) {
+  const uint32_t a = (uint32_t)w0, b = (uint32_t)(w0 >> 32), c = (uint32_t)w1, d = (uint32_t)(w1 >> 32);
+  const uint32_t t = s & 31;
+  const bool hiw = s >= 32;
+  const uint32_t x0 = hiw ? b : a, x1 = hiw ? c : b, x2 = hiw ? d : c;
+  const uint32_t lo = __funnelshift_r(x0, x1, t);   // (x1:x0) >> t, low word
+  const uint32_t hi = __funnelshift_r(x1, x2, t);
+  return ((uint64_t)hi << 32) | lo;
+}
+
+// A CTA takes tiles of WARPS * WT positions. All its threads gather, pack and
+// hash the tile (one barrier); then each warp evaluates the windows of its own
+// WT-position sub-tile and writes its minimizers in order. STAGED: into the
+// sub-tile's own WT slots of a staging array plus a count (a scan and a
+// compaction pass order them; tiles are strided over CTAs). Otherwise:
+// directly to their final place, found by a decoupled look-back over
+// sub-tiles taken from a ticket.
+template <int WARPS, typename KT, bool WIDE, bool STAGED>
+__global__ void __launch_bounds__(WARPS * 32) sketch_kernel(SketchArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int BLOCK = WARPS * 32;
+  const int WT = a.T;                         // owned positions per warp
+  const int T = WARPS * WT;                   // owned positions per CTA tile
   const SketchJob& J = a.job;
-  const int T = a.T;
   const int k = J.k, w = J.w;
-  const int n_keys = T + 2 * (w - 1);
-  const int n_codes = n_keys + k - 1;
-  const int n_win = T + w - 1;
-  // shared layout
-  uint64_t* keys = reinterpret_cast<uint64_t*>(smem);
-  uint64_t* A1 = keys + n_keys;
-  uint64_t* A2 = A1 + n_keys;
-  uint32_t* own_seg = reinterpret_cast<uint32_t*>(A2 + n_keys);
-  uint32_t* own_pos = own_seg + T;
-  uint8_t* codes = reinterpret_cast<uint8_t*>(own_pos + T);
-  uint8_t* zb = codes + ((n_codes + 15) & ~15);
-  __shared__ uint64_t s_tile_base;
-  __shared__ uint32_t s_tile;
-  __shared__ uint32_t s_warp_cnt[BLOCK / 32];
+  const TileLayout Lt = tile_layout(WARPS, WT, k, w, (int)sizeof(KT));
+  const int n_keys = Lt.n_keys, n_codes = Lt.n_codes, n_groups = Lt.n_groups, n_chunks = Lt.n_chunks;
+  const int n_win_w = Lt.n_win_w;
+  const int n_keys_w = WT + 2 * (w - 1);
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  KT* K = reinterpret_cast<KT*>(smem);
+  KT* SM = reinterpret_cast<KT*>(smem + Lt.off_sm) + (size_t)wid * 2 * n_keys_w;  // this warp's
+  KT* SX = SM + n_keys_w;
+  uint64_t* F = reinterpret_cast<uint64_t*>(smem + Lt.off_f);
+  uint64_t* Cw = reinterpret_cast<uint64_t*>(smem + Lt.off_c);
+  int2* cst = reinterpret_cast<int2*>(smem + Lt.off_cst);
+  uint32_t* Nm = reinterpret_cast<uint32_t*>(smem + Lt.off_nm);
+  uint8_t* zb = smem + Lt.off_zb;
+  uint8_t* sel = smem + Lt.off_sel + wid * WT;
+  uint16_t* list = reinterpret_cast<uint16_t*>(smem + Lt.off_list) + wid * WT;
+  __shared__ uint32_t s_tile, s_gt;
+  __shared__ uint64_t bnd[kBndCache + 1];    // seg_voff[g_tile + i], i <= kBndCache
 
   const uint64_t mask = (k >= 32) ? ~0ULL : ((1ULL << (2 * k)) - 1);
-  const int rc_shift = 2 * (k - 1);
+  const uint64_t nmask = (1ULL << k) - 1;
+  const uint32_t top_shift = 64 - 2 * k;
   const int p = J.pat.p, x = J.pat.x;
-  const int tid = threadIdx.x;
+  const KT PALIN = palin_mark<KT>();
+  const unsigned FULL = 0xffffffffu;
+  const unsigned lt = (1u << lane) - 1u;
+  const uint64_t n_sub = a.n_tiles;           // status words are per warp sub-tile
 
-  while (true) {
-    if (tid == 0) s_tile = atomicAdd(a.ticket, 1u);
+  for (uint32_t iter = 0;; ++iter) {
+    if (tid == 0) {
+      const uint32_t tile = STAGED ? blockIdx.x + iter * gridDim.x : atomicAdd(a.ticket, 1u);
+      s_tile = tile;
+      s_gt = (uint64_t)tile * WARPS < n_sub ? a.tile_seg[tile] : 0;
+    }
     __syncthreads();
     const uint64_t tile = s_tile;
-    if (tile >= a.n_tiles) break;
+    if (tile * WARPS >= n_sub) break;
+    for (int i = tid; i <= kBndCache; i += BLOCK)
+      bnd[i] = J.seg_voff[min((uint64_t)s_gt + i, (uint64_t)J.n_seg)];
+    __syncthreads();
     const int64_t A = (int64_t)(tile * (uint64_t)T);
     const int64_t v_first = A - (w - 1);
+    const uint32_t g_tile = s_gt;
 
-    // ---- 1. gather codes (contiguous chunk per thread, incremental segment walk)
-    {
-      const int R = (n_codes + BLOCK - 1) / BLOCK;
-      const int lo = tid * R;
-      const int hi = min(lo + R, n_codes);
-      bool have = false;
-      uint32_t g = 0, j = 0, q = 0, r = 0;
-      uint64_t gend = 0;
-      SegDesc d{};
-      for (int u = lo; u < hi; ++u) {
-        const int64_t v = v_first + u;
-        uint32_t code = 4;
-        const bool own = (u >= w - 1) && (u < w - 1 + T);
-        uint32_t oseg = 0xFFFFFFFFu, opos = 0xFFFFFFFFu;
-        if (v >= 0 && (uint64_t)v < J.V) {
-          if (!have || (uint64_t)v >= gend) {
-            g = have ? g + 1 : find_segment(J.seg_voff, J.n_seg, (uint64_t)v);
-            d = J.segs[g];
-            const uint64_t gstart = J.seg_voff[g];
-            gend = J.seg_voff[g + 1];
-            j = (uint32_t)((uint64_t)v - gstart);
-            q = j / (uint32_t)x;
-            r = j - q * (uint32_t)x;
-            have = true;
+    // ---- 1. gather 8 bases per thread step, pack 2-bit codes with shuffles
+    for (int c0 = 0; c0 < n_chunks; c0 += BLOCK) {
+      if (c0 + wid * 32 >= n_chunks) break;   // warp-uniform: whole warp idle
+      const int c = c0 + tid;
+      const bool act = c < n_chunks;
+      const int64_t v0 = v_first + 8 * (int64_t)c;
+      uint32_t f16 = 0, c16 = 0, n8 = 0xFFu;
+      int2 state = make_int2(-1, 0);
+      if (act && v0 + 8 > 0 && v0 < (int64_t)J.V && 8 * c < n_codes) {
+        n8 = 0;
+        const uint64_t vs = v0 < 0 ? 0 : (uint64_t)v0;
+        // segment of vs: bisect the cached boundaries of the tile's first
+        // kBndCache segments (global memory only past them)
+        uint32_t g;
+        if (bnd[kBndCache] <= vs && g_tile + kBndCache < J.n_seg) {
+          uint32_t lo = g_tile + kBndCache, hi = J.n_seg;
+          while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (J.seg_voff[mid] <= vs) lo = mid; else hi = mid;
           }
-          oseg = g;
-          if (j < d.m) {
-            const uint64_t orig = (uint64_t)d.shift + (uint64_t)p * q + (uint64_t)J.pat.off[r];
-            code = base_code(__ldg(J.bytes + d.byte_off + orig));
-            if (code == 4 && (d.flags & kSegCapped) && J.read_flag) J.read_flag[d.read] = 1u;
-            opos = (uint32_t)orig;
+          g = lo;
+        } else {
+          uint32_t lo = 0, hi = kBndCache;
+          while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (bnd[mid] <= vs) lo = mid; else hi = mid;
           }
-          ++j;
-          if (++r == (uint32_t)x) { r = 0; ++q; }
+          g = g_tile + lo;
         }
-        codes[u] = (uint8_t)code;
-        if (own) {
-          own_seg[u - (w - 1)] = oseg;
-          own_pos[u - (w - 1)] = opos;
-        }
-      }
-    }
-    __syncthreads();
-
-    // ---- 2. canonical k-mer keys (rolling per contiguous chunk)
-    {
-      const int R = (n_keys + BLOCK - 1) / BLOCK;
-      const int lo = tid * R;
-      const int hi = min(lo + R, n_keys);
-      if (lo < hi) {
-        uint64_t fwd = 0, rev = 0;
-        int run = 0;
-        for (int c = lo; c < lo + k - 1; ++c) {
-          const uint32_t b = codes[c];
-          if (b == 4) { run = 0; fwd = 0; rev = 0; }
-          else {
-            ++run;
-            fwd = ((fwd << 2) | b) & mask;
-            rev = (rev >> 2) | ((uint64_t)(3u - b) << rc_shift);
-          }
-        }
-        for (int i = lo; i < hi; ++i) {
-          const uint32_t b = codes[i + k - 1];
-          if (b == 4) { run = 0; fwd = 0; rev = 0; }
-          else {
-            ++run;
-            fwd = ((fwd << 2) | b) & mask;
-            rev = (rev >> 2) | ((uint64_t)(3u - b) << rc_shift);
-          }
-          uint64_t kk = 0;
-          uint8_t z = 0;
-          if (run >= k) {
-            if (fwd == rev) kk = kPalin;
-            else {
-              z = rev < fwd;
-              kk = wang_mix<WIDE>(z ? rev : fwd, mask) + 1;
-            }
-          }
-          keys[i] = kk;
-          zb[i] = z;
-        }
-      }
-    }
-    __syncthreads();
-
-    // ---- 3. window minima (van Herk / Gil-Werman), M -> A1[0 .. n_win)
-    {
-      const int nb = (n_keys + w - 1) / w;
-      for (int b = tid; b < nb; b += BLOCK) {
-        const int s = b * w, e = min(s + w, n_keys);
-        uint64_t m = ~0ULL;
-        for (int i = s; i < e; ++i) { m = min(m, keys[i]); A2[i] = m; }     // prefix
-        m = ~0ULL;
-        for (int i = e - 1; i >= s; --i) { m = min(m, keys[i]); A1[i] = m; } // suffix
-      }
-      __syncthreads();
-      for (int i = tid; i < n_win; i += BLOCK) A1[i] = min(A1[i], A2[i + w - 1]);
-    }
-    __syncthreads();
-
-    // ---- 4. largest window minimum containing each owned position
-    {
-      const int nb = (n_win + w - 1) / w;
-      for (int b = tid; b < nb; b += BLOCK) {
-        const int s = b * w, e = min(s + w, n_win);
-        uint64_t m = 0;
-        for (int i = s; i < e; ++i) { m = max(m, A1[i]); A2[i] = m; }      // prefix max
-        m = 0;
-        for (int i = e - 1; i >= s; --i) { m = max(m, A1[i]); A1[i] = m; } // suffix max (in place)
-      }
-    }
-    __syncthreads();
-
-    // ---- 5. select and compact in stream order
-    const int RO = T / BLOCK;  // T is a multiple of BLOCK
-    const int o_lo = tid * RO;
-    uint32_t sel = 0;  // bit i: owned position o_lo + i is a minimizer (RO <= 32)
-    int cnt = 0;
-    for (int i = 0; i < RO; ++i) {
-      const int o = o_lo + i;
-      const uint64_t kk = keys[o + w - 1];
-      const uint64_t mx = max(A1[o], A2[o + w - 1]);
-      if (kk != 0 && kk != kPalin && kk == mx) { sel |= 1u << i; ++cnt; }
-    }
-    // block exclusive scan of cnt
-    const int lane = tid & 31, wid = tid >> 5;
-    int incl = cnt;
+        SegDesc d = J.segs[g];
+        uint64_t gend = J.seg_voff[g + 1];
+        uint32_t j = (uint32_t)(vs - J.seg_voff[g]);
+        // (segment, index of the chunk's first base in it + 8): biased because
+        // the stream's first chunk starts before position 0
+        state = make_int2((int)g, (int)(j + 8u - (uint32_t)((int64_t)vs - v0)));
+        uint32_t q = j / (uint32_t)x, r = j - q * (uint32_t)x;
+        const uint8_t* src = J.bytes + d.byte_off;
 #pragma unroll
-    for (int dd = 1; dd < 32; dd <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, incl, dd);
-      if (lane >= dd) incl += y;
-    }
-    if (lane == 31) s_warp_cnt[wid] = (uint32_t)incl;
-    __syncthreads();
-    if (tid == 0) {
-      uint32_t run = 0;
-      for (int i = 0; i < BLOCK / 32; ++i) { const uint32_t c = s_warp_cnt[i]; s_warp_cnt[i] = run; run += c; }
-      // decoupled look-back for the tile's global offset
-      const uint64_t tile_cnt = run;
-      uint64_t excl = 0;
-      if (tile == 0) {
-        st_release_u64(a.tile_status, kFlagIncl | tile_cnt);
-      } else {
-        st_release_u64(a.tile_status + tile, kFlagAgg | tile_cnt);
-        int64_t pr = (int64_t)tile - 1;
-        while (pr >= 0) {
-          uint64_t s;
-          uint32_t spins = 0;
-          while (true) {
-            s = ld_acquire_u64(a.tile_status + pr);
-            if (s & (kFlagAgg | kFlagIncl)) break;
-            if (++spins > kSpinLimit) { atomicExch(a.err, GOD_ETIMEOUT); s = kFlagIncl; break; }
-            __nanosleep(64);
+        for (int dd = 0; dd < 8; ++dd) {
+          const int64_t v = v0 + dd;
+          uint32_t code = 4;
+          if (v >= 0 && (uint64_t)v < J.V && 8 * c + dd < n_codes) {
+            if ((uint64_t)v >= gend) {
+              ++g;
+              d = J.segs[g];
+              src = J.bytes + d.byte_off;
+              gend = J.seg_voff[g + 1];
+              j = 0; q = 0; r = 0;
+            }
+            if (j < d.m) {
+              code = base_code(__ldg(src + d.shift + (uint64_t)p * q + (uint32_t)J.pat.off[r]));
+              if (code == 4 && (d.flags & kSegCapped) && J.read_flag) J.read_flag[d.read] = 1u;
+            }
+            ++j;
+            if (++r == (uint32_t)x) { r = 0; ++q; }
           }
-          excl += s & kValMask;
-          if (s & kFlagIncl) break;
-          --pr;
+          if (code < 4) {
+            f16 |= code << (14 - 2 * dd);
+            c16 |= (3u - code) << (2 * dd);
+          } else {
+            n8 |= 1u << dd;
+          }
         }
-        st_release_u64(a.tile_status + tile, kFlagIncl | (excl + tile_cnt));
       }
-      if (tile == a.n_tiles - 1) *a.total = excl + tile_cnt;
-      s_tile_base = excl;
+      if (act) cst[c] = state;
+      // four consecutive lanes hold the four chunks of one 32-base group
+      // (n_chunks is a multiple of 4: a group is all active or all idle)
+      const int part = lane & 3;
+      uint64_t fw = (uint64_t)f16 << (48 - 16 * part);
+      uint64_t cw = (uint64_t)c16 << (16 * part);
+      uint32_t nw = n8 << (8 * part);
+      fw |= __shfl_xor_sync(FULL, fw, 1);
+      cw |= __shfl_xor_sync(FULL, cw, 1);
+      nw |= __shfl_xor_sync(FULL, nw, 1);
+      fw |= __shfl_xor_sync(FULL, fw, 2);
+      cw |= __shfl_xor_sync(FULL, cw, 2);
+      nw |= __shfl_xor_sync(FULL, nw, 2);
+      if (act && part == 0) {
+        F[c >> 2] = fw;
+        Cw[c >> 2] = cw;
+        Nm[c >> 2] = nw;
+      }
+    }
+    if (tid == 0) {  // one spare group so that every k-mer reads two words
+      F[n_groups] = 0;
+      Cw[n_groups] = 0;
+      Nm[n_groups] = 0xFFFFFFFFu;
     }
     __syncthreads();
-    uint64_t dst = s_tile_base + s_warp_cnt[wid] + (uint64_t)(incl - cnt);
-    if (sel) {
-      for (int i = 0; i < RO; ++i) {
-        if (!(sel >> i & 1u)) continue;
-        const int o = o_lo + i;
-        if (dst < J.out_cap) {
-          MinRec rec;
-          rec.key = keys[o + w - 1] - 1;
-          rec.pos = own_pos[o];
-          rec.segz = (own_seg[o] << 1) | zb[o + w - 1];
-          J.out[dst] = rec;
+
+    // ---- 2. canonical k-mer keys, one position per thread (funnel shifts)
+    for (int i0 = 0; i0 < n_keys; i0 += BLOCK) {
+      if (i0 + wid * 32 >= n_keys) break;
+      const int i = i0 + tid;
+      if (i < n_keys) {
+        const int g = i >> 5, b = i & 31;
+        const uint64_t nn = (((uint64_t)Nm[g + 1] << 32) | Nm[g]) >> b;
+        KT kk = 0;
+        uint8_t z = 0;
+        if ((nn & nmask) == 0) {
+          const uint64_t fwd = take64_be(F[g], F[g + 1], 2 * b) >> top_shift;
+          const uint64_t rev = take64_le(Cw[g], Cw[g + 1], 2 * b) & mask;
+          if (fwd == rev) {
+            kk = PALIN;
+          } else {
+            z = rev < fwd;
+            kk = (KT)(wang_mix<WIDE>(z ? rev : fwd, mask) + 1);
+          }
         }
-        if (J.seg_cnt) atomicAdd(J.seg_cnt + own_seg[o], 1u);
-        ++dst;
+        K[i] = kk;
+        zb[i] = z;
       }
     }
-    __syncthreads();  // shared arrays are rewritten by the next tile
+    __syncthreads();
+
+    // ---- 3. this warp's window minima over keys [wo, wo + n_keys_w) of the
+    // tile, wo = 256 * warp (van Herk / Gil-Werman: lane = one block of w
+    // keys; suffix minima backwards, prefix minima forwards with the next
+    // block's running prefix taken from the next lane).
+    const int wo = wid * WT;
+    const KT* Kw = K + wo;
+    {
+      const int nb = (n_keys_w + w - 1) / w;
+      for (int gb = 0; gb < nb; gb += 31) {
+        const int b = gb + lane;
+        const int s = b * w;
+        const bool live = b < nb;
+        KT m = PALIN;
+        for (int t = w - 1; t >= 0; --t) {
+          const int i = s + t;
+          if (live && i < n_keys_w) { m = min(m, Kw[i]); SM[i] = m; }
+        }
+        __syncwarp();
+        KT pm = PALIN;
+        for (int t = 0; t < w; ++t) {
+          const int i = s + t;
+          const KT kv = (live && i < n_keys_w) ? Kw[i] : PALIN;
+          const KT nxt = __shfl_down_sync(FULL, pm, 1);   // next block's prefix over offsets < t
+          if (lane < 31 && live && i < n_win_w && t) SM[i] = min(SM[i], nxt);
+          pm = min(pm, kv);
+        }
+        __syncwarp();
+      }
+    }
+
+    // ---- 4. largest window minimum covering each owned position; the test
+    {
+      const int nb = (n_win_w + w - 1) / w;
+      for (int gb = 0; gb < nb; gb += 31) {
+        const int b = gb + lane;
+        const int s = b * w;
+        const bool live = b < nb;
+        KT m = 0;
+        for (int t = w - 1; t >= 0; --t) {
+          const int i = s + t;
+          if (live && i < n_win_w) { m = max(m, SM[i]); SX[i] = m; }
+        }
+        __syncwarp();
+        KT px = 0;
+        for (int t = 0; t < w; ++t) {
+          const int i = s + t;
+          const KT mv = (live && i < n_win_w) ? SM[i] : (KT)0;
+          const KT nxt = __shfl_down_sync(FULL, px, 1);
+          if (lane < 31 && live && i < WT) {
+            const KT mx = t == 0 ? SX[i] : max(SX[i], nxt);
+            const KT kk = Kw[i + w - 1];
+            sel[i] = (kk != 0 && kk != PALIN && kk == mx) ? 1 : 0;
+          }
+          px = max(px, mv);
+        }
+        __syncwarp();
+      }
+    }
+
+    // ---- 5. compact the selected positions, then ordered output through a
+    // warp-parallel decoupled look-back over sub-tiles
+    uint32_t cnt = 0;
+    for (int o0 = 0; o0 < WT; o0 += 32) {
+      const bool f = o0 + lane < WT && sel[o0 + lane] != 0;
+      const unsigned bal = __ballot_sync(FULL, f);
+      if (f) list[cnt + __popc(bal & lt)] = (uint16_t)(o0 + lane);
+      cnt += __popc(bal);
+    }
+    __syncwarp();
+    const uint64_t sub = tile * WARPS + wid;
+    uint64_t excl = 0;
+    if (STAGED && sub < n_sub) {
+      if (lane == 0) a.sub_cnt[sub] = cnt;
+      for (uint32_t li = lane; li < cnt; li += 32) {
+        const int u = wo + list[li] + w - 1;       // base / k-mer index inside the tile
+        const int2 st = cst[u >> 3];
+        uint32_t g = (uint32_t)st.x;
+        int64_t jj = (int64_t)(uint32_t)st.y - 8 + (u & 7);
+        SegDesc d = J.segs[g];
+        while (jj > (int64_t)d.m) {
+          jj -= (int64_t)d.m + 1;
+          d = J.segs[++g];
+        }
+        const uint32_t qq = (uint32_t)jj / (uint32_t)x;
+        MinRec rec;
+        rec.key = (uint64_t)K[u] - 1;
+        rec.pos = d.shift + (uint32_t)p * qq + (uint32_t)J.pat.off[(uint32_t)jj - qq * (uint32_t)x];
+        rec.segz = (g << 1) | zb[u];
+        a.staging[sub * (uint64_t)WT + li] = rec;
+        if (J.seg_cnt) atomicAdd(J.seg_cnt + g, 1u);
+      }
+    } else if (!STAGED && sub < n_sub) {
+      if (sub == 0) {
+        if (lane == 0) st_release_u64(a.tile_status, kFlagIncl | cnt);
+      } else {
+        if (lane == 0) st_release_u64(a.tile_status + sub, kFlagAgg | cnt);
+        int64_t pbase = (int64_t)sub - 1;
+        while (true) {
+          const int64_t idx = pbase - lane;
+          uint64_t s = idx >= 0 ? ld_acquire_u64(a.tile_status + idx) : kFlagIncl;
+          uint32_t spins = 0;
+          while (!__all_sync(FULL, (s & (kFlagAgg | kFlagIncl)) != 0)) {
+            if (++spins > kSpinLimit) {
+              if (lane == 0) atomicExch(a.err, GOD_ETIMEOUT);
+              if (!(s & (kFlagAgg | kFlagIncl))) s = kFlagIncl;
+              break;
+            }
+            __nanosleep(32);
+            if (!(s & (kFlagAgg | kFlagIncl))) s = ld_acquire_u64(a.tile_status + idx);
+          }
+          const unsigned im = __ballot_sync(FULL, (s & kFlagIncl) != 0);
+          if (im) {
+            const int first = __ffs(im) - 1;          // nearest predecessor with an inclusive prefix
+            excl += warp_sum_u64(lane <= first ? (s & kValMask) : 0);
+            break;
+          }
+          excl += warp_sum_u64(s & kValMask);
+          pbase -= 32;
+        }
+        if (lane == 0) st_release_u64(a.tile_status + sub, kFlagIncl | (excl + cnt));
+      }
+      if (lane == 0 && sub == n_sub - 1) *a.total = excl + cnt;
+      for (uint32_t li = lane; li < cnt; li += 32) {
+        const int u = wo + list[li] + w - 1;       // base / k-mer index inside the tile
+        const int2 st = cst[u >> 3];
+        uint32_t g = (uint32_t)st.x;
+        int64_t jj = (int64_t)(uint32_t)st.y - 8 + (u & 7);
+        SegDesc d = J.segs[g];
+        while (jj > (int64_t)d.m) {
+          jj -= (int64_t)d.m + 1;
+          d = J.segs[++g];
+        }
+        const uint32_t qq = (uint32_t)jj / (uint32_t)x;
+        const uint32_t orig = d.shift + (uint32_t)p * qq + (uint32_t)J.pat.off[(uint32_t)jj - qq * (uint32_t)x];
+        const uint64_t at = excl + li;
+        if (at < J.out_cap) {
+          MinRec rec;
+          rec.key = (uint64_t)K[u] - 1;
+          rec.pos = orig;
+          rec.segz = (g << 1) | zb[u];
+          J.out[at] = rec;
+        }
+        if (J.seg_cnt) atomicAdd(J.seg_cnt + g, 1u);
+      }
+    }
+    __syncthreads();  // the tile's shared memory is rewritten by the next tile
   }
 }
 
-size_t sketch_smem_bytes(int T, int k, int w) {
-  const size_t n_keys = (size_t)T + 2 * (w - 1);
-  const size_t n_codes = n_keys + k - 1;
-  return n_keys * 8 * 3 + (size_t)T * 8 + ((n_codes + 15) & ~(size_t)15) + n_keys + 16;
-}
-
-template <int BLOCK, bool WIDE>
-int launch_sketch_t(const SketchArgs& a, size_t smem, cudaStream_t st) {
-  auto sketch = sketch_kernel<BLOCK, WIDE>;
+template <int WARPS, typename KT, bool WIDE, bool STAGED>
+int launch_sketch_kt(const SketchArgs& a, cudaStream_t st) {
+  auto sketch = sketch_kernel<WARPS, KT, WIDE, STAGED>;
+  const size_t smem = tile_layout(WARPS, a.T, a.job.k, a.job.w, (int)sizeof(KT)).bytes;
   GOD_CK(cudaFuncSetAttribute(sketch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
-  GOD_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sketch, BLOCK, smem));
-  if (per_sm < 1) per_sm = 1;
+  GOD_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sketch, WARPS * 32, smem));
+  if (per_sm < 1) {
+    set_error("sketch: tile workspace does not fit in shared memory");
+    return GOD_EINVAL;
+  }
   const uint64_t want = (uint64_t)num_sms() * per_sm;
-  const unsigned grid = (unsigned)std::min<uint64_t>(want, a.n_tiles);
-  GOD_LAUNCH(sketch, grid, BLOCK, smem, st, a);
+  const uint64_t ctas_needed = (a.n_tiles + WARPS - 1) / WARPS;
+  const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(want, ctas_needed));
+  GOD_LAUNCH(sketch, grid, WARPS * 32, smem, st, a);
   return GOD_OK;
+}
+
+template <int WARPS, bool STAGED>
+int launch_sketch_w(const SketchArgs& a, cudaStream_t st) {
+  if (a.job.k > 16) return launch_sketch_kt<WARPS, uint64_t, true, STAGED>(a, st);
+  if (a.job.k <= 15) return launch_sketch_kt<WARPS, uint32_t, false, STAGED>(a, st);
+  return launch_sketch_kt<WARPS, uint64_t, false, STAGED>(a, st);
+}
+
+// First segment of every CTA tile (the segment holding its first halo base).
+__global__ void tile_first_segment(const uint64_t* voff, uint32_t n_seg, uint64_t V, uint64_t T, int w,
+                                   uint64_t n_ctiles, uint32_t* tseg) {
+  for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < n_ctiles; t += (uint64_t)gridDim.x * blockDim.x) {
+    const int64_t vf = (int64_t)(t * T) - (w - 1);
+    const uint64_t v0 = vf < 0 ? 0 : (uint64_t)vf;
+    tseg[t] = v0 < V ? find_segment(voff, n_seg, v0) : 0;
+  }
+}
+
+// n_tiles in SketchArgs counts warp sub-tiles of a.T positions; the caller
+// provides tile_seg for ceil(n_tiles / warps) CTA tiles (or it is computed here).
+template <bool STAGED>
+int launch_sketch(SketchArgs a, const SketchTune& tn, cudaStream_t st) {
+  const int warps = tn.threads / 32;
+  const uint64_t n_ctiles = (a.n_tiles + warps - 1) / warps;
+  GOD_LAUNCH(tile_first_segment, (unsigned)std::min<uint64_t>((n_ctiles + 255) / 256, 65535), 256, 0, st,
+             a.job.seg_voff, a.job.n_seg, a.job.V, (uint64_t)a.T * warps, a.job.w, n_ctiles, a.tile_seg);
+  switch (tn.threads) {
+    case 128: return launch_sketch_w<4, STAGED>(a, st);
+    default: return launch_sketch_w<8, STAGED>(a, st);
+  }
+}
+
+// Staged records of each sub-tile -> their ordered place (warp per sub-tile).
+__global__ void compact_staged(const MinRec* __restrict__ staging, const uint32_t* __restrict__ sub_cnt,
+                               const uint64_t* __restrict__ sub_off, uint64_t n_sub, int WT, MinRec* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x / 32);
+  for (uint64_t sub = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) / 32; sub < n_sub; sub += warps) {
+    const uint32_t c = sub_cnt[sub];
+    const uint64_t o = sub_off[sub];
+    const MinRec* src = staging + sub * (uint64_t)WT;
+    for (uint32_t i = lane; i < c; i += 32) out[o + i] = src[i];
+  }
+}
+
+SketchTune clamp_tune(SketchTune tn, int k, int w) {
+  if (tn.threads != 128 && tn.threads != 256) tn.threads = 256;
+  tn.tile = sub_tile_for(tn.threads / 32, k, w);
+  return tn;
 }
 
 }  // namespace
 
 SketchTune default_sketch_tune(int k, int w) {
-  (void)k;
-  (void)w;
-  return SketchTune{2048, 256};
+  return SketchTune{sub_tile_for(8, k, w), 256};
 }
 
-int run_sketch(const SketchJob& job, cudaStream_t st, uint64_t* total, const SketchTune* tune) {
-  SketchTune tn = tune ? *tune : default_sketch_tune(job.k, job.w);
-  if (tn.threads != 128 && tn.threads != 256 && tn.threads != 512) tn.threads = 256;
-  if (tn.tile < tn.threads || tn.tile % tn.threads || tn.tile / tn.threads > 32) tn.tile = tn.threads * 8;
+int run_sketch(const SketchJob& job, cudaStream_t st, DBuf<MinRec>& out, uint64_t* total, const SketchTune* tune) {
+  const SketchTune tn = clamp_tune(tune ? *tune : default_sketch_tune(job.k, job.w), job.k, job.w);
   *total = 0;
-  if (job.V == 0) return GOD_OK;
-  const uint64_t n_tiles = (job.V + tn.tile - 1) / tn.tile;
-  // status words + ticket + total + error flag in one allocation
-  DBuf<unsigned long long> ws;
-  GOD_TRY(ws.alloc(n_tiles + 4, st));
-  GOD_CK(cudaMemsetAsync(ws.p, 0, (n_tiles + 4) * sizeof(unsigned long long), st));
-  SketchArgs a;
+  if (job.V == 0) return out.alloc(0, st);
+  const int warps = tn.threads / 32;
+  const uint64_t n_sub = (job.V + tn.tile - 1) / tn.tile;
+  const uint64_t n_ctiles = (n_sub + warps - 1) / warps;
+  DBuf<MinRec> staging;
+  DBuf<uint32_t> sub_cnt, tseg;
+  DBuf<uint64_t> sub_off;
+  GOD_TRY(staging.alloc(n_sub * (uint64_t)tn.tile, st));
+  GOD_TRY(sub_cnt.alloc(n_sub, st));
+  GOD_TRY(sub_off.alloc(n_sub + 1, st));
+  GOD_TRY(tseg.alloc(n_ctiles, st));
+  SketchArgs a{};
   a.job = job;
-  a.tile_status = ws.p;
-  a.ticket = reinterpret_cast<unsigned int*>(ws.p + n_tiles);
-  a.total = ws.p + n_tiles + 1;
-  a.err = reinterpret_cast<int*>(ws.p + n_tiles + 2);
-  a.n_tiles = n_tiles;
+  a.tile_seg = tseg.p;
+  a.staging = staging.p;
+  a.sub_cnt = sub_cnt.p;
+  a.n_tiles = n_sub;
   a.T = tn.tile;
-  const size_t smem = sketch_smem_bytes(tn.tile, job.k, job.w);
-  const bool wide = job.k > 16;
-  int rc;
-  if (tn.threads == 128) rc = wide ? launch_sketch_t<128, true>(a, smem, st) : launch_sketch_t<128, false>(a, smem, st);
-  else if (tn.threads == 512) rc = wide ? launch_sketch_t<512, true>(a, smem, st) : launch_sketch_t<512, false>(a, smem, st);
-  else rc = wide ? launch_sketch_t<256, true>(a, smem, st) : launch_sketch_t<256, false>(a, smem, st);
-  if (rc != GOD_OK) return rc;
-  unsigned long long host[3];
-  GOD_CK(cudaMemcpyAsync(host, ws.p + n_tiles + 1, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+  GOD_TRY(launch_sketch<true>(a, tn, st));
+  GOD_TRY(exclusive_scan_u32(sub_cnt.p, sub_off.p, n_sub, st));
+  uint64_t tot = 0;
+  GOD_CK(cudaMemcpyAsync(&tot, sub_off.p + n_sub, 8, cudaMemcpyDeviceToHost, st));
   GOD_CK(cudaStreamSynchronize(st));
-  *total = host[0];
-  // algorithmic bytes: every patterned base read once, every record written once
-  prof_add_work("sketch", (double)(job.V - job.n_seg) + 16.0 * (double)host[0], (double)(job.V - job.n_seg));
-  if ((int)(host[1] & 0xFFFFFFFFu) == GOD_ETIMEOUT) {
-    set_error("sketch: ordered-compaction look-back wait gave up");
-    return GOD_ETIMEOUT;
+  *total = tot;
+  GOD_TRY(out.alloc(tot, st));
+  if (tot) {
+    const uint64_t blocks = std::min<uint64_t>((n_sub * 32 + 255) / 256, (uint64_t)num_sms() * 16);
+    GOD_LAUNCH(compact_staged, (unsigned)blocks, 256, 0, st, staging.p, sub_cnt.p, sub_off.p, n_sub, tn.tile,
+               out.p);
   }
+  // algorithmic bytes: every patterned base read once, every record written once
+  prof_add_work("sketch", (double)(job.V - job.n_seg) + 16.0 * (double)tot, (double)(job.V - job.n_seg));
   return GOD_OK;
 }
 
@@ -404,9 +638,15 @@ int run_sketch(const SketchJob& job, cudaStream_t st, uint64_t* total, const Ske
 namespace god {
 namespace {
 
-constexpr uint64_t kNoAllocWords = 32768;                 // 256 KiB of scratch per device
+constexpr uint64_t kNoAllocWords = 262144;                // 2 MiB of scratch per device
 constexpr uint64_t kNoAllocTail = 8;                      // segment descriptor + offsets
-constexpr uint64_t kNoAllocMaxTiles = kNoAllocWords - kNoAllocTail - 4;
+// Status words (one per sub-tile) + 4 counters + first segment per CTA tile
+// (u32, two per word) must fit before the tail. The smallest sub-tile over all
+// k <= 28, w <= 255 is sub_tile_for(8, 28, 255) = 184 positions; with it the
+// bound below admits patterned lengths up to GOD_NOALLOC_MAX_PATTERNED.
+inline bool noalloc_fits(uint64_t n_tiles, uint64_t n_ctiles) {
+  return n_tiles + 4 + (n_ctiles + 1) / 2 <= kNoAllocWords - kNoAllocTail;
+}
 static __device__ __align__(256) unsigned long long g_noalloc_scratch[kNoAllocWords];
 
 constexpr int kMaxDevices = 64;
@@ -461,11 +701,12 @@ extern "C" int god_sketch_noalloc(const uint8_t* d_seq, uint64_t len, const char
     set_error("god_sketch_noalloc: sequence must be shorter than 2^32 bases");
     return GOD_EINVAL;
   }
-  const SketchTune tn{2048, 256};
+  const SketchTune tn = default_sketch_tune(k, w);
   const uint64_t m = patterned_len(P, len, shift);
   const uint64_t V = m + 1;
   const uint64_t n_tiles = (V + tn.tile - 1) / tn.tile;
-  if (n_tiles > kNoAllocMaxTiles) {
+  const uint64_t n_ctiles = (n_tiles + tn.threads / 32 - 1) / (tn.threads / 32);
+  if (m > GOD_NOALLOC_MAX_PATTERNED || !noalloc_fits(n_tiles, n_ctiles)) {
     set_error("god_sketch_noalloc: patterned length exceeds GOD_NOALLOC_MAX_PATTERNED");
     return GOD_EINVAL;
   }
@@ -492,14 +733,13 @@ extern "C" int god_sketch_noalloc(const uint8_t* d_seq, uint64_t len, const char
   a.job.out = reinterpret_cast<MinRec*>(d_out);   // same 16-byte layout; segment 0 leaves z alone
   a.job.out_cap = cap;
   a.tile_status = scratch;
+  a.tile_seg = reinterpret_cast<uint32_t*>(scratch + n_tiles + 4);
   a.ticket = reinterpret_cast<unsigned int*>(scratch + n_tiles);
   a.total = scratch + n_tiles + 1;
   a.err = reinterpret_cast<int*>(scratch + n_tiles + 2);
   a.n_tiles = n_tiles;
   a.T = tn.tile;
-  const size_t smem = sketch_smem_bytes(tn.tile, k, w);
-  const int lrc = (k > 16) ? launch_sketch_t<256, true>(a, smem, st) : launch_sketch_t<256, false>(a, smem, st);
-  if (lrc != GOD_OK) return lrc;
+  GOD_TRY(launch_sketch<false>(a, tn, st));
   unsigned long long host[2] = {0, 0};
   GOD_CK(cudaMemcpyAsync(host, scratch + n_tiles + 1, sizeof host, cudaMemcpyDeviceToHost, st));
   GOD_CK(cudaStreamSynchronize(st));

@@ -9,6 +9,8 @@ This file is collected last so that a failure here stops a run only after
 every other test has run.
 """
 import ctypes as C
+import os
+import re
 
 import numpy as np
 import pytest
@@ -16,6 +18,9 @@ import pytest
 from paper_2211_08157_gb300 import synth
 
 pytestmark = pytest.mark.gpu
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "god.h")
+MAX_PATTERNED = int(re.search(r"#define GOD_NOALLOC_MAX_PATTERNED (\d+)ULL", open(HEADER).read()).group(1))
 
 
 @pytest.fixture(scope="module")
@@ -68,7 +73,7 @@ def test_noalloc_reports_size_and_limits(env):
     d = torch.zeros(16, dtype=torch.uint8, device="cuda")
     o = torch.zeros((1, 4), dtype=torch.int32, device="cuda")
     cnt = C.c_uint64()
-    too_long = 2 * 67084287 + 10                      # pattern 10 keeps half of it
+    too_long = 2 * MAX_PATTERNED + 10                 # pattern 10 keeps half of it
     assert L.god_sketch_noalloc(d.data_ptr(), too_long, b"10", 0, 15, 10, o.data_ptr(), 1, C.byref(cnt), None) == -1
     assert b"GOD_NOALLOC_MAX_PATTERNED" in L.god_last_error()
     # host memory is refused (it would need a device copy)
