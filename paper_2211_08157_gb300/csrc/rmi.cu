@@ -99,6 +99,100 @@ __global__ void root_reduce_adam(const float* __restrict__ partial, int blocks, 
   }
 }
 
+// Least-squares readout: with the hidden layer fixed, the output layer (W2,
+// b2) that minimises the MSE solves the normal equations G w = r with
+// G = sum phi phi^T, r = sum phi y, phi = (relu(W1 x + b1), 1). Entries of the
+// upper triangle of G, then r, are accumulated in double per sample chunk
+// (fixed order: deterministic).
+constexpr int kGramN = H + 1;
+constexpr int kGramTri = kGramN * (kGramN + 1) / 2;
+constexpr int kGramE = kGramTri + kGramN;
+constexpr int kGramChunks = 64;
+
+__device__ __forceinline__ double phi_of(const float* th, float x, int h) {
+  if (h == H) return 1.0;
+  return (double)fmaxf(__fmaf_rn(th[h], x, th[H + h]), 0.0f);
+}
+
+__global__ void root_gram_partial(const float* __restrict__ theta, const float* __restrict__ xs,
+                                  const float* __restrict__ ys, uint64_t n, double* __restrict__ partial) {
+  __shared__ float th[NP];
+  for (int i = threadIdx.x; i < NP; i += blockDim.x) th[i] = theta[i];
+  __syncthreads();
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= kGramE) return;
+  int i = 0, j = 0;
+  if (e < kGramTri) {  // row-major upper triangle
+    int rem = e;
+    while (rem >= kGramN - i) { rem -= kGramN - i; ++i; }
+    j = i + rem;
+  } else {
+    i = e - kGramTri;
+    j = -1;  // r entry
+  }
+  const uint64_t chunk = (n + kGramChunks - 1) / kGramChunks;
+  const uint64_t lo = blockIdx.y * chunk, hi = min(n, lo + chunk);
+  double acc = 0.0;
+  for (uint64_t t = lo; t < hi; ++t) {
+    const float x = xs[t];
+    const double a = phi_of(th, x, i);
+    acc += j >= 0 ? a * phi_of(th, x, j) : a * (double)ys[t];
+  }
+  partial[(uint64_t)blockIdx.y * kGramE + e] = acc;
+}
+
+// One thread: sum the chunk partials in order, add a tiny ridge, Cholesky,
+// solve, and write (W2, b2) into theta.
+__global__ void root_gram_solve(const double* __restrict__ partial, float* __restrict__ theta) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double G[kGramN][kGramN], r[kGramN];
+  for (int e = 0; e < kGramE; ++e) {
+    double v = 0.0;
+    for (int c = 0; c < kGramChunks; ++c) v += partial[(uint64_t)c * kGramE + e];
+    if (e < kGramTri) {
+      int i = 0, rem = e;
+      while (rem >= kGramN - i) { rem -= kGramN - i; ++i; }
+      G[i][i + rem] = v;
+      G[i + rem][i] = v;
+    } else {
+      r[e - kGramTri] = v;
+    }
+  }
+  double tr = 0.0;
+  for (int i = 0; i < kGramN; ++i) tr += G[i][i];
+  const double ridge = 1e-12 * tr / kGramN + 1e-300;
+  for (int i = 0; i < kGramN; ++i) G[i][i] += ridge;
+  // Cholesky G = L L^T in place (lower triangle)
+  for (int j = 0; j < kGramN; ++j) {
+    double d = G[j][j];
+    for (int k2 = 0; k2 < j; ++k2) d -= G[j][k2] * G[j][k2];
+    d = d > 0 ? sqrt(d) : 1e-150;
+    G[j][j] = d;
+    for (int i = j + 1; i < kGramN; ++i) {
+      double v = G[i][j];
+      for (int k2 = 0; k2 < j; ++k2) v -= G[i][k2] * G[j][k2];
+      G[i][j] = v / d;
+    }
+  }
+  double y[kGramN];
+  for (int i = 0; i < kGramN; ++i) {
+    double v = r[i];
+    for (int k2 = 0; k2 < i; ++k2) v -= G[i][k2] * y[k2];
+    y[i] = v / G[i][i];
+  }
+  for (int i = kGramN - 1; i >= 0; --i) {
+    double v = y[i];
+    for (int k2 = i + 1; k2 < kGramN; ++k2) v -= G[k2][i] * y[k2];
+    y[i] = v / G[i][i];
+  }
+  for (int h = 0; h < H; ++h) theta[2 * H + h] = (float)y[h];
+  theta[3 * H] = (float)y[H];
+}
+
+__global__ void copy_floats(const float* src, float* dst, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+}
+
 // Training samples: evenly spaced ranks r_i = floor(i * U / S); x = normalised
 // key with the lookup's own FP32 expression; y = r_i / U.
 __global__ void make_samples(const uint64_t* keys, uint64_t U, uint64_t S, uint64_t kmin, float inv_span, float* xs,
@@ -298,9 +392,23 @@ int build_rmi(god_index* idx, cudaStream_t st) {
     GOD_CK(cudaMemsetAsync(m2.p, 0, NP * sizeof(float), st));
     const float inv_n = 1.0f / (float)S;
     const int steps = P.rmi_train_steps;
+    // 1. exact least-squares output layer over the fixed ReLU features
+    DBuf<double> gpart;
+    DBuf<float> best, gbest;
+    GOD_TRY(gpart.alloc((size_t)kGramChunks * kGramE, st));
+    GOD_TRY(best.alloc(NP, st));
+    GOD_TRY(gbest.alloc(NP + 1, st));
+    GOD_LAUNCH(root_gram_partial, dim3((kGramE + 255) / 256, kGramChunks), 256, 0, st, theta.p, xs.p, ys.p, S,
+               gpart.p);
+    GOD_LAUNCH(root_gram_solve, 1, 32, 0, st, gpart.p, theta.p);
+    GOD_LAUNCH(copy_floats, 1, 128, 0, st, theta.p, best.p, NP);
+    GOD_LAUNCH(root_grad_partial, kGradBlocks, kGradThreads, 0, st, theta.p, xs.p, ys.p, S, inv_n, partial.p);
+    GOD_LAUNCH(root_reduce_adam, 1, 128, 0, st, partial.p, kGradBlocks, gbest.p, nullptr, nullptr, nullptr, 0, 0.0f,
+               0, inv_n);
+    // 2. Adam on all parameters with the forward/backward kernels (small steps:
+    //    the start is already near the optimum)
     for (int it = 1; it <= steps; ++it) {
-      // learning rate: 1e-2 decayed to 1e-4 (cosine)
-      const float lr = 1e-4f + 0.5f * (1e-2f - 1e-4f) * (1.0f + cosf(3.14159265f * (float)(it - 1) / (float)steps));
+      const float lr = 1e-7f + 0.5f * (1e-5f - 1e-7f) * (1.0f + cosf(3.14159265f * (float)(it - 1) / (float)steps));
       GOD_LAUNCH(root_grad_partial, kGradBlocks, kGradThreads, 0, st, theta.p, xs.p, ys.p, S, inv_n, partial.p);
       GOD_LAUNCH(root_reduce_adam, 1, 128, 0, st, partial.p, kGradBlocks, gout.p, theta.p, m1.p, m2.p, it, lr, 1,
                  inv_n);
@@ -309,8 +417,16 @@ int build_rmi(god_index* idx, cudaStream_t st) {
     GOD_LAUNCH(root_grad_partial, kGradBlocks, kGradThreads, 0, st, theta.p, xs.p, ys.p, S, inv_n, partial.p);
     GOD_LAUNCH(root_reduce_adam, 1, 128, 0, st, partial.p, kGradBlocks, gout.p, nullptr, nullptr, nullptr, 0, 0.0f, 0,
                inv_n);
-    GOD_CK(cudaMemcpyAsync(th, theta.p, sizeof(th), cudaMemcpyDeviceToHost, st));
+    float lsq_loss = 0.0f;
     GOD_CK(cudaMemcpyAsync(&loss, gout.p + NP, sizeof(float), cudaMemcpyDeviceToHost, st));
+    GOD_CK(cudaMemcpyAsync(&lsq_loss, gbest.p + NP, sizeof(float), cudaMemcpyDeviceToHost, st));
+    GOD_CK(cudaStreamSynchronize(st));
+    if (!(loss <= lsq_loss)) {  // keep the better of the two (also when Adam produced NaN)
+      loss = lsq_loss;
+      GOD_CK(cudaMemcpyAsync(th, best.p, sizeof(th), cudaMemcpyDeviceToHost, st));
+    } else {
+      GOD_CK(cudaMemcpyAsync(th, theta.p, sizeof(th), cudaMemcpyDeviceToHost, st));
+    }
     GOD_CK(cudaStreamSynchronize(st));
     for (int h = 0; h < H; ++h) { R.W1[h] = th[h]; R.b1[h] = th[H + h]; R.W2[h] = th[2 * H + h]; }
     R.b2 = th[3 * H];
