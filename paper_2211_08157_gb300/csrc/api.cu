@@ -281,7 +281,7 @@ void god_params_init(god_params* p) {
   p->rmi_leaf_bits = 0;
   p->rmi_eps_max = 64;
   p->rmi_root = GOD_ROOT_MLP;
-  p->rmi_train_steps = 400;
+  p->rmi_train_steps = 64;
   p->rmi_train_samples = 65536;
   p->tune = 0;
 }

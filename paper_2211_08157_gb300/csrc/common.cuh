@@ -150,6 +150,19 @@ struct SketchJob {
 // position) in `out`, allocated to exactly *total records. job.out / out_cap
 // are not used.
 int run_sketch(const SketchJob& job, cudaStream_t st, DBuf<MinRec>& out, uint64_t* total, const SketchTune* tune);
+
+// The same pass without the final compaction: sub-tile s holds sub_cnt[s]
+// records at staging[s * WT ...] in stream order; sub_off is their exclusive
+// scan (n_sub + 1 entries, sub_off[n_sub] = total). For callers that fuse the
+// compaction into their own next pass.
+struct StagedSketch {
+  DBuf<MinRec> staging;
+  DBuf<uint32_t> sub_cnt;
+  DBuf<uint64_t> sub_off;
+  uint64_t n_sub = 0, total = 0;
+  int WT = 0;
+};
+int run_sketch_staged(const SketchJob& job, cudaStream_t st, StagedSketch& out, const SketchTune* tune);
 SketchTune default_sketch_tune(int k, int w);
 
 // ------------------------------------------------------------------ scan

@@ -95,39 +95,6 @@ __global__ void ht_insert(const uint64_t* keys, const uint32_t* start, uint64_t 
 }  // namespace
 
 // ------------------------------------------------------------------ lookups
-__device__ __forceinline__ uint64_t ht_find(const ulonglong2* __restrict__ ht, uint64_t mask, uint64_t key) {
-  uint64_t slot = key & mask;
-  for (uint64_t probe = 0; probe <= mask; ++probe) {
-    const ulonglong2 e = __ldg(ht + slot);
-    if (e.x == key) return e.y;
-    if (e.x == kEmptyKey) return 0;
-    slot = (slot + 1) & mask;
-  }
-  return 0;
-}
-
-__device__ __forceinline__ uint64_t rmi_find(const DeviceIndex& di, const RmiRoot& R, uint64_t key) {
-  if (key < R.kmin || key > R.kmax) return ht_find(di.ht, di.ht_mask, key);
-  const uint32_t leaf = rmi_root_leaf(R, key);
-  const RmiLeaf L = di.leaves[leaf];
-  const uint32_t eps = (uint32_t)(L.base_eps >> 56);
-  if (eps > di.eps_max) return ht_find(di.ht, di.ht_mask, key);
-  const int64_t pred = rmi_leaf_pred(L.slope, L.icept, L.base_eps & ((1ULL << 56) - 1), key);
-  int64_t lo = pred - (int64_t)eps, hi = pred + (int64_t)eps;
-  if (lo < 0) lo = 0;
-  if (hi > (int64_t)di.n_keys - 1) hi = (int64_t)di.n_keys - 1;
-  while (lo <= hi) {  // last-mile binary search inside [pred - eps, pred + eps]
-    const int64_t mid = (lo + hi) >> 1;
-    const uint64_t km = __ldg(di.keys + mid);
-    if (km == key) {
-      const uint32_t s = __ldg(di.start + mid), e = __ldg(di.start + mid + 1);
-      return (uint64_t)s | ((uint64_t)(e - s) << 32);
-    }
-    if (km < key) lo = mid + 1; else hi = mid - 1;
-  }
-  return 0;
-}
-
 template <int VIA>
 __global__ void __launch_bounds__(kThreads) lookup_kernel(DeviceIndex di, const uint64_t* keys, size_t stride_words,
                                                           uint64_t n, uint64_t* out) {

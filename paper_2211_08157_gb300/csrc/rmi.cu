@@ -107,7 +107,7 @@ __global__ void root_reduce_adam(const float* __restrict__ partial, int blocks, 
 constexpr int kGramN = H + 1;
 constexpr int kGramTri = kGramN * (kGramN + 1) / 2;
 constexpr int kGramE = kGramTri + kGramN;
-constexpr int kGramChunks = 64;
+constexpr int kGramChunks = 256;
 
 __device__ __forceinline__ double phi_of(const float* th, float x, int h) {
   if (h == H) return 1.0;
@@ -141,12 +141,13 @@ __global__ void root_gram_partial(const float* __restrict__ theta, const float* 
   partial[(uint64_t)blockIdx.y * kGramE + e] = acc;
 }
 
-// One thread: sum the chunk partials in order, add a tiny ridge, Cholesky,
-// solve, and write (W2, b2) into theta.
+// Sum the chunk partials in order (one thread per entry), then one thread
+// adds a tiny ridge, factors G = L L^T (Cholesky, shared memory) and solves;
+// (W2, b2) go into theta.
 __global__ void root_gram_solve(const double* __restrict__ partial, float* __restrict__ theta) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double G[kGramN][kGramN], r[kGramN];
-  for (int e = 0; e < kGramE; ++e) {
+  __shared__ double G[kGramN][kGramN + 1];
+  __shared__ double r[kGramN], y[kGramN];
+  for (int e = threadIdx.x; e < kGramE; e += blockDim.x) {
     double v = 0.0;
     for (int c = 0; c < kGramChunks; ++c) v += partial[(uint64_t)c * kGramE + e];
     if (e < kGramTri) {
@@ -158,11 +159,12 @@ __global__ void root_gram_solve(const double* __restrict__ partial, float* __res
       r[e - kGramTri] = v;
     }
   }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
   double tr = 0.0;
   for (int i = 0; i < kGramN; ++i) tr += G[i][i];
   const double ridge = 1e-12 * tr / kGramN + 1e-300;
   for (int i = 0; i < kGramN; ++i) G[i][i] += ridge;
-  // Cholesky G = L L^T in place (lower triangle)
   for (int j = 0; j < kGramN; ++j) {
     double d = G[j][j];
     for (int k2 = 0; k2 < j; ++k2) d -= G[j][k2] * G[j][k2];
@@ -174,7 +176,6 @@ __global__ void root_gram_solve(const double* __restrict__ partial, float* __res
       G[i][j] = v / d;
     }
   }
-  double y[kGramN];
   for (int i = 0; i < kGramN; ++i) {
     double v = r[i];
     for (int k2 = 0; k2 < i; ++k2) v -= G[i][k2] * y[k2];
@@ -230,33 +231,31 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
-// One warp per leaf: least squares in double over the leaf's keys (ranks are
-// ascending inside the run, so the first key is the smallest = base), then the
+// One thread per leaf: least squares in double over the leaf's keys (ranks
+// ascend inside the run, so the first key is the smallest = base), then the
 // error bound with the FP32 prediction of the lookup path.
 __global__ void fit_leaves(const uint64_t* __restrict__ keys, const uint64_t* __restrict__ ranks,
                            const uint32_t* __restrict__ lo, const uint32_t* __restrict__ hi, uint32_t n_leaves,
                            RmiLeaf* leaves, unsigned long long* stats) {
-  const int lane = threadIdx.x & 31;
-  const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x / 32);
-  for (uint64_t l = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) / 32; l < n_leaves; l += warps) {
+  unsigned long long eps_sum = 0;
+  for (uint64_t l = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; l < n_leaves; l += (uint64_t)gridDim.x * blockDim.x) {
     const uint32_t b = lo[l], e = hi[l];
     RmiLeaf out;
     if (e <= b) {
       out.base_eps = 0;
       out.slope = 0.0f;
       out.icept = 0.0f;
-      if (lane == 0) leaves[l] = out;
+      leaves[l] = out;
       continue;
     }
     const uint64_t base = keys[ranks[b]];
     double sx = 0, sy = 0, sxx = 0, sxy = 0;
-    for (uint32_t i = b + lane; i < e; i += 32) {
+    for (uint32_t i = b; i < e; ++i) {
       const uint64_t r = ranks[i];
       const double dx = (double)(keys[r] - base);
       const double dy = (double)r;
       sx += dx; sy += dy; sxx += dx * dx; sxy += dx * dy;
     }
-    sx = warp_sum_d(sx); sy = warp_sum_d(sy); sxx = warp_sum_d(sxx); sxy = warp_sum_d(sxy);
     const double c = (double)(e - b);
     double slope = 0.0, icept = sy / c;
     const double den = c * sxx - sx * sx;
@@ -266,38 +265,54 @@ __global__ void fit_leaves(const uint64_t* __restrict__ keys, const uint64_t* __
     }
     const float fs = (float)slope, fi = (float)icept;
     uint64_t mx = 0;
-    for (uint32_t i = b + lane; i < e; i += 32) {
+    for (uint32_t i = b; i < e; ++i) {
       const uint64_t r = ranks[i];
       const int64_t p = rmi_leaf_pred(fs, fi, base, keys[r]);
       const int64_t d = p > (int64_t)r ? p - (int64_t)r : (int64_t)r - p;
       mx = max(mx, (uint64_t)d);
     }
-#pragma unroll
-    for (int d = 16; d >= 1; d >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, d));
     const uint64_t eps = mx > 255 ? 255 : mx;
-    if (lane == 0) {
-      out.base_eps = (base & ((1ULL << 56) - 1)) | (eps << 56);
-      out.slope = fs;
-      out.icept = fi;
-      leaves[l] = out;
-      atomicAdd(&stats[0], (unsigned long long)mx * (e - b));   // key-weighted eps sum
-      atomicMax(&stats[1], (unsigned long long)mx);             // (all leaves)
-    }
+    out.base_eps = (base & ((1ULL << 56) - 1)) | (eps << 56);
+    out.slope = fs;
+    out.icept = fi;
+    leaves[l] = out;
+    eps_sum += (unsigned long long)mx * (e - b);   // key-weighted eps sum
   }
+#pragma unroll
+  for (int d = 16; d >= 1; d >>= 1) eps_sum += __shfl_xor_sync(0xffffffffu, eps_sum, d);
+  if ((threadIdx.x & 31) == 0 && eps_sum) atomicAdd(&stats[0], eps_sum);
 }
 
 __global__ void leaf_stats(const RmiLeaf* leaves, const uint32_t* lo, const uint32_t* hi, uint32_t n_leaves,
                            uint32_t eps_max, unsigned long long* stats) {
+  unsigned long long fl = 0, fk = 0, mx = 0;
   for (uint64_t l = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; l < n_leaves; l += (uint64_t)gridDim.x * blockDim.x) {
     const uint32_t cnt = hi[l] > lo[l] ? hi[l] - lo[l] : 0;
     const uint32_t eps = (uint32_t)(leaves[l].base_eps >> 56);
     if (cnt > 0 && eps > eps_max) {
-      atomicAdd(&stats[3], 1ull);          // fallback leaves
-      atomicAdd(&stats[4], (unsigned long long)cnt);  // keys in fallback leaves
+      fl += 1;      // fallback leaves
+      fk += cnt;    // keys in fallback leaves
     } else if (cnt > 0) {
-      atomicMax(&stats[5], (unsigned long long)eps);  // largest bound used
+      mx = max(mx, (unsigned long long)eps);  // largest bound used
     }
   }
+#pragma unroll
+  for (int d = 16; d >= 1; d >>= 1) {
+    fl += __shfl_xor_sync(0xffffffffu, fl, d);
+    fk += __shfl_xor_sync(0xffffffffu, fk, d);
+    mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, d));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (fl) atomicAdd(&stats[3], fl);
+    if (fk) atomicAdd(&stats[4], fk);
+    if (mx) atomicMax(&stats[5], mx);
+  }
+}
+
+// flag = 1 when the routed leaf ids of the (ascending) keys ever decrease.
+__global__ void leaf_monotone(const uint64_t* leaf, uint64_t U, int* flag) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i + 1 < U; i += (uint64_t)gridDim.x * blockDim.x)
+    if (leaf[i] > leaf[i + 1]) *flag = 1;
 }
 
 void init_root(RmiRoot* R, int kind) {
@@ -400,7 +415,7 @@ int build_rmi(god_index* idx, cudaStream_t st) {
     GOD_TRY(gbest.alloc(NP + 1, st));
     GOD_LAUNCH(root_gram_partial, dim3((kGramE + 255) / 256, kGramChunks), 256, 0, st, theta.p, xs.p, ys.p, S,
                gpart.p);
-    GOD_LAUNCH(root_gram_solve, 1, 32, 0, st, gpart.p, theta.p);
+    GOD_LAUNCH(root_gram_solve, 1, 256, 0, st, gpart.p, theta.p);
     GOD_LAUNCH(copy_floats, 1, 128, 0, st, theta.p, best.p, NP);
     GOD_LAUNCH(root_grad_partial, kGradBlocks, kGradThreads, 0, st, theta.p, xs.p, ys.p, S, inv_n, partial.p);
     GOD_LAUNCH(root_reduce_adam, 1, 128, 0, st, partial.p, kGradBlocks, gbest.p, nullptr, nullptr, nullptr, 0, 0.0f,
@@ -446,12 +461,21 @@ int build_rmi(god_index* idx, cudaStream_t st) {
   GOD_TRY(stats.alloc(8, st));
   const unsigned g = (unsigned)std::min<uint64_t>((U + 255) / 256, (uint64_t)num_sms() * 32);
   GOD_LAUNCH(route_keys, g, 256, 0, st, d_root.p, idx->d_keys, U, lk.p, rv.p);
-  GOD_TRY(radix_sort_pairs(lk.p, rv.p, U, bits, st));
+  // Keys of a leaf are contiguous in rank order when the routing is monotone
+  // (the usual case); only otherwise group them by leaf with a sort.
+  DBuf<int> nonmono;
+  GOD_TRY(nonmono.alloc(1, st));
+  GOD_CK(cudaMemsetAsync(nonmono.p, 0, sizeof(int), st));
+  GOD_LAUNCH(leaf_monotone, g, 256, 0, st, lk.p, U, nonmono.p);
+  int h_nonmono = 0;
+  GOD_CK(cudaMemcpyAsync(&h_nonmono, nonmono.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  GOD_CK(cudaStreamSynchronize(st));
+  if (h_nonmono) GOD_TRY(radix_sort_pairs(lk.p, rv.p, U, bits, st));
   GOD_CK(cudaMemsetAsync(lo.p, 0, n_leaves * sizeof(uint32_t), st));
   GOD_CK(cudaMemsetAsync(hi.p, 0, n_leaves * sizeof(uint32_t), st));
   GOD_CK(cudaMemsetAsync(stats.p, 0, 8 * sizeof(unsigned long long), st));
   GOD_LAUNCH(leaf_bounds, g, 256, 0, st, lk.p, U, lo.p, hi.p);
-  const unsigned gl = (unsigned)std::min<uint64_t>(((uint64_t)n_leaves * 32 + 255) / 256, (uint64_t)num_sms() * 32);
+  const unsigned gl = (unsigned)std::min<uint64_t>(((uint64_t)n_leaves + 255) / 256, (uint64_t)num_sms() * 32);
   GOD_LAUNCH(fit_leaves, gl, 256, 0, st, idx->d_keys, rv.p, lo.p, hi.p, n_leaves, leaves.p, stats.p);
   GOD_LAUNCH(leaf_stats, (unsigned)std::min<uint64_t>((n_leaves + 255) / 256, 4096), 256, 0, st, leaves.p, lo.p, hi.p,
              n_leaves, idx->params.rmi_eps_max, stats.p);

@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "rmi_device.cuh"
 
 namespace god {
 namespace {
@@ -47,6 +48,26 @@ struct RecSet {
 struct RecSets {
   RecSet s[3];
 };
+// Constant indices only: a runtime index into a parameter array would copy it
+// to local memory.
+__device__ __forceinline__ RecSet pick_set(const RecSets& S, uint32_t k) {
+  return k == 0 ? S.s[0] : (k == 1 ? S.s[1] : S.s[2]);
+}
+
+constexpr int kTinyCap = 16;            // anchors per read for the thread path
+
+// Appends i to list (unordered) with one atomic per warp.
+__device__ __forceinline__ void warp_append(bool f, uint32_t i, uint32_t* list, unsigned long long* counter) {
+  const unsigned am = __activemask();
+  const unsigned bal = __ballot_sync(am, f);
+  if (!bal) return;
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(am) - 1;
+  unsigned long long base = 0;
+  if (lane == leader) base = atomicAdd(counter, (unsigned long long)__popc(bal));
+  base = __shfl_sync(am, base, leader);
+  if (f) list[base + __popc(bal & ((1u << lane) - 1u))] = i;
+}
 
 __global__ void make_pa_segments(const uint64_t* __restrict__ offs, uint32_t n, PatternInfo P, uint32_t cap,
                                  SegDesc* __restrict__ segs, uint32_t* __restrict__ vlen, int* err) {
@@ -91,55 +112,70 @@ __global__ void make_list_segments(const uint64_t* __restrict__ offs, const uint
   }
 }
 
-__device__ __forceinline__ uint64_t shift_sum(const RecSet& S, uint64_t g, uint32_t t) {
+// Sum of index counts over a segment's first t records (t = 0: all) and over
+// all of its records.
+__device__ __forceinline__ void shift_sums(const RecSet& S, uint64_t g, uint32_t t, uint64_t* sum_t, uint64_t* sum_all) {
   const uint64_t beg = S.seg_off[g];
   const uint32_t c = S.seg_cnt[g];
-  const uint32_t use = t ? min(c, t) : c;
-  uint64_t sum = 0;
-  for (uint32_t j = 0; j < use; ++j) sum += S.sc[beg + j] >> 32;
-  return sum;
+  uint64_t a = 0, b = 0;
+  for (uint32_t j = 0; j < c; ++j) {
+    const uint64_t v = S.sc[beg + j] >> 32;
+    b += v;
+    if (!t || j < t) a += v;
+  }
+  *sum_t = a;
+  *sum_all = b;
 }
 
-// Pattern alignment over the PA pass: one thread per read.
+// Pattern alignment over the PA pass: one thread per read. The chosen shift's
+// whole-segment count is the read's anchor count when that segment was not a
+// prefix; otherwise the read joins the seeding-pass list (or the fallback list
+// when its prefix held an N).
 __global__ void pa_select(uint32_t n, int p, uint32_t t, const SegDesc* __restrict__ segs, RecSet S,
                           const uint32_t* __restrict__ need_full, uint32_t* __restrict__ shift,
-                          uint32_t* __restrict__ src, uint32_t* __restrict__ seed_seg, uint32_t* __restrict__ fb_flag,
-                          uint32_t* __restrict__ p2_flag) {
+                          uint32_t* __restrict__ src, uint32_t* __restrict__ seed_seg, uint64_t* __restrict__ read_cnt,
+                          uint32_t* __restrict__ fb_list, uint32_t* __restrict__ p2_list,
+                          unsigned long long* __restrict__ counts) {
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    bool fb = false, p2 = false;
     if (need_full[i]) {
-      fb_flag[i] = 1;
-      p2_flag[i] = 0;
+      fb = true;
       src[i] = kSrcFB;
-      continue;
+    } else {
+      uint64_t best = 0, all_a = 0;
+      uint32_t a = 0;
+      for (int s = 0; s < p; ++s) {
+        uint64_t st, sa;
+        shift_sums(S, i * p + s, t, &st, &sa);
+        if (s == 0 || st > best) { best = st; a = (uint32_t)s; all_a = sa; }
+      }
+      shift[i] = a;
+      seed_seg[i] = (uint32_t)(i * p + a);
+      p2 = segs[i * p + a].flags & kSegCapped;
+      src[i] = p2 ? kSrcP2 : kSrcPA;
+      if (!p2) read_cnt[i] = all_a;
     }
-    uint64_t best = 0;
-    uint32_t a = 0;
-    for (int s = 0; s < p; ++s) {
-      const uint64_t sum = shift_sum(S, i * p + s, t);
-      if (sum > best) { best = sum; a = (uint32_t)s; }
-    }
-    shift[i] = a;
-    const bool capped = segs[i * p + a].flags & kSegCapped;
-    src[i] = capped ? kSrcP2 : kSrcPA;
-    seed_seg[i] = (uint32_t)(i * p + a);
-    fb_flag[i] = 0;
-    p2_flag[i] = capped;
+    warp_append(fb, (uint32_t)i, fb_list, counts + 0);
+    warp_append(p2, (uint32_t)i, p2_list, counts + 1);
   }
 }
 
 // Pattern alignment of fallback reads over their full-length segments.
 __global__ void pa_select_list(const uint32_t* __restrict__ list, uint32_t nl, int p, uint32_t t, RecSet S,
-                               uint32_t* __restrict__ shift, uint32_t* __restrict__ seed_seg) {
+                               uint32_t* __restrict__ shift, uint32_t* __restrict__ seed_seg,
+                               uint64_t* __restrict__ read_cnt) {
   for (uint64_t li = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; li < nl; li += (uint64_t)gridDim.x * blockDim.x) {
-    uint64_t best = 0;
+    uint64_t best = 0, all_a = 0;
     uint32_t a = 0;
     for (int s = 0; s < p; ++s) {
-      const uint64_t sum = shift_sum(S, li * p + s, t);
-      if (sum > best) { best = sum; a = (uint32_t)s; }
+      uint64_t st, sa;
+      shift_sums(S, li * p + s, t, &st, &sa);
+      if (s == 0 || st > best) { best = st; a = (uint32_t)s; all_a = sa; }
     }
     const uint32_t i = list[li];
     shift[i] = a;
     seed_seg[i] = (uint32_t)(li * p + a);
+    read_cnt[i] = all_a;
   }
 }
 
@@ -148,37 +184,34 @@ __global__ void set_seed_seg_list(const uint32_t* __restrict__ list, uint32_t nl
     seed_seg[list[li]] = (uint32_t)li;
 }
 
-// Anchors per read = sum of index counts of its seeding minimizers (warp per read).
-__global__ void count_anchors(uint32_t n, RecSets sets, const uint32_t* __restrict__ src,
-                              const uint32_t* __restrict__ seed_seg, uint64_t* __restrict__ read_cnt) {
+// Anchors of the listed reads = sum of index counts of their seeding-pass
+// minimizers (segment li of the set belongs to list[li]; warp per read).
+__global__ void count_anchors_list(const uint32_t* __restrict__ list, uint32_t nl, RecSet S,
+                                   uint64_t* __restrict__ read_cnt) {
   const int lane = threadIdx.x & 31;
   const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x / 32);
-  for (uint64_t i = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) / 32; i < n; i += warps) {
-    const RecSet& S = sets.s[src[i]];
-    const uint32_t g = seed_seg[i];
-    const uint64_t beg = S.seg_off[g];
-    const uint32_t c = S.seg_cnt[g];
+  for (uint64_t li = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) / 32; li < nl; li += warps) {
+    const uint64_t beg = S.seg_off[li];
+    const uint32_t c = S.seg_cnt[li];
     uint64_t sum = 0;
     for (uint32_t j = lane; j < c; j += 32) sum += S.sc[beg + j] >> 32;
 #pragma unroll
     for (int d = 16; d >= 1; d >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, d);
-    if (lane == 0) read_cnt[i] = sum;
+    if (lane == 0) read_cnt[list[li]] = sum;
   }
 }
 
-__global__ void classify_reads(uint32_t n, const uint64_t* __restrict__ read_off, uint32_t* __restrict__ small,
-                               uint32_t* __restrict__ large) {
+// Reads by anchor-list length: tiny (thread path), small (warp path), large
+// (CTA path). Lists are unordered; every read writes its own output range.
+__global__ void classify_reads(uint32_t n, const uint64_t* __restrict__ read_off, uint32_t* __restrict__ tiny,
+                               uint32_t* __restrict__ small, uint32_t* __restrict__ large,
+                               unsigned long long* __restrict__ counts) {
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t c = read_off[i + 1] - read_off[i];
-    small[i] = (c > 0 && c <= kSmallCap) ? 1u : 0u;
-    large[i] = c > kSmallCap ? 1u : 0u;
+    warp_append(c > 0 && c <= kTinyCap, (uint32_t)i, tiny, counts + 0);
+    warp_append(c > kTinyCap && c <= kSmallCap, (uint32_t)i, small, counts + 1);
+    warp_append(c > kSmallCap, (uint32_t)i, large, counts + 2);
   }
-}
-
-__global__ void scatter_list(const uint32_t* __restrict__ flag, const uint64_t* __restrict__ pos, uint64_t n,
-                             uint32_t* __restrict__ list) {
-  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
-    if (flag[i]) list[pos[i]] = (uint32_t)i;
 }
 
 __device__ __forceinline__ uint64_t anchor_key(uint64_t entry, uint32_t read_pos, uint32_t z) {
@@ -192,6 +225,60 @@ __device__ __forceinline__ void store_anchor(god_anchor* out, uint32_t read, uin
   v.z = (uint32_t)(key >> 32);
   v.w = (uint32_t)(key & 1u);
   *reinterpret_cast<uint4*>(out) = v;
+}
+
+// Tiny anchor lists (<= 16): one thread per read gathers them into registers
+// (compile-time slots) and sorts them with a 16-wide bitonic network.
+__device__ __forceinline__ void cswap(uint64_t& a, uint64_t& b, bool up) {
+  const uint64_t lo = a < b ? a : b, hi = a < b ? b : a;
+  a = up ? lo : hi;
+  b = up ? hi : lo;
+}
+
+__global__ void __launch_bounds__(kT) fill_sort_tiny(RecSets sets, const uint32_t* __restrict__ src,
+                                                     const uint32_t* __restrict__ seed_seg,
+                                                     const uint64_t* __restrict__ read_off,
+                                                     const uint32_t* __restrict__ list, uint32_t nl,
+                                                     const uint64_t* __restrict__ ent, god_anchor* __restrict__ out) {
+  for (uint64_t li = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; li < nl; li += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t i = list[li];
+    const uint64_t off = read_off[i];
+    const uint32_t n = (uint32_t)(read_off[i + 1] - off);
+    const RecSet S = pick_set(sets, src[i]);
+    const uint32_t g = seed_seg[i];
+    const uint64_t beg = S.seg_off[g];
+    const uint32_t cnt = S.seg_cnt[g];
+    uint64_t v[kTinyCap];
+#pragma unroll
+    for (int q = 0; q < kTinyCap; ++q) v[q] = ~0ULL;
+    uint32_t fill = 0;
+    for (uint32_t r = 0; r < cnt; ++r) {
+      const uint64_t sc = S.sc[beg + r];
+      const uint32_t c = (uint32_t)(sc >> 32);
+      if (!c) continue;
+      const MinRec m = S.rec[beg + r];
+      const uint32_t start = (uint32_t)sc;
+      for (uint32_t e = 0; e < c; ++e, ++fill) {
+        const uint64_t key = anchor_key(__ldg(ent + start + e), m.pos, m.segz & 1u);
+#pragma unroll
+        for (int q = 0; q < kTinyCap; ++q) v[q] = (q == (int)fill) ? key : v[q];
+      }
+    }
+#pragma unroll
+    for (int kk = 2; kk <= kTinyCap; kk <<= 1) {
+#pragma unroll
+      for (int j = kk >> 1; j > 0; j >>= 1) {
+#pragma unroll
+        for (int q = 0; q < kTinyCap; ++q) {
+          const int r2 = q ^ j;
+          if (r2 > q) cswap(v[q], v[r2], (q & kk) == 0);
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kTinyCap; ++q)
+      if (q < (int)n) store_anchor(out + off + q, i, v[q]);
+  }
 }
 
 // Short anchor lists: one warp per read builds the list in shared memory and
@@ -209,7 +296,7 @@ __global__ void __launch_bounds__(kT) fill_sort_small(RecSets sets, const uint32
     const uint32_t i = list[li];
     const uint64_t off = read_off[i];
     const uint32_t n = (uint32_t)(read_off[i + 1] - off);
-    const RecSet& S = sets.s[src[i]];
+    const RecSet S = pick_set(sets, src[i]);
     const uint32_t g = seed_seg[i];
     const uint64_t beg = S.seg_off[g];
     const uint32_t cnt = S.seg_cnt[g];
@@ -348,7 +435,7 @@ __global__ void __launch_bounds__(kLargeThreads) fill_sort_large(RecSets sets, c
     const uint32_t i = list[li];
     const uint64_t off = read_off[i];
     const uint64_t n = read_off[i + 1] - off;
-    const RecSet& S = sets.s[src[i]];
+    const RecSet S = pick_set(sets, src[i]);
     const uint32_t g = seed_seg[i];
     const uint64_t beg = S.seg_off[g];
     const uint32_t cnt = S.seg_cnt[g];
@@ -394,18 +481,31 @@ __global__ void __launch_bounds__(kLargeThreads) fill_sort_large(RecSets sets, c
   }
 }
 
-// ---- host helpers
-int compact_flags(const uint32_t* flags, uint64_t n, DBuf<uint32_t>& list, uint64_t* count, cudaStream_t st) {
-  DBuf<uint64_t> pos;
-  GOD_TRY(pos.alloc(n + 1, st));
-  GOD_TRY(exclusive_scan_u32(flags, pos.p, n, st));
-  uint64_t c = 0;
-  GOD_CK(cudaMemcpyAsync(&c, pos.p + n, 8, cudaMemcpyDeviceToHost, st));
-  GOD_CK(cudaStreamSynchronize(st));
-  *count = c;
-  GOD_TRY(list.alloc(c, st));
-  if (c && n) GOD_LAUNCH(scatter_list, grid_for(n), kT, 0, st, flags, pos.p, n, list.p);
-  return GOD_OK;
+// Staged sketch output -> ordered records, each looked up in the index on
+// the way (warp per sketch sub-tile; the lookup result is start | count << 32).
+template <int VIA>
+__global__ void __launch_bounds__(kT) compact_lookup(const MinRec* __restrict__ staging,
+                                                     const uint32_t* __restrict__ sub_cnt,
+                                                     const uint64_t* __restrict__ sub_off, uint64_t n_sub, int WT,
+                                                     DeviceIndex di, MinRec* __restrict__ out,
+                                                     uint64_t* __restrict__ sc) {
+  __shared__ RmiRoot R;
+  if (VIA == 1) {
+    if (threadIdx.x == 0) R = *di.root;
+    __syncthreads();
+  }
+  const int lane = threadIdx.x & 31;
+  const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x / 32);
+  for (uint64_t sub = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) / 32; sub < n_sub; sub += warps) {
+    const uint32_t c = sub_cnt[sub];
+    const uint64_t o = sub_off[sub];
+    const MinRec* src = staging + sub * (uint64_t)WT;
+    for (uint32_t i = lane; i < c; i += 32) {
+      const MinRec r = src[i];
+      out[o + i] = r;
+      sc[o + i] = VIA == 1 ? rmi_find(di, R, r.key) : ht_find(di.ht, di.ht_mask, r.key);
+    }
+  }
 }
 
 // One record set: sketch + lookup + per-segment offsets.
@@ -421,13 +521,21 @@ struct SetBufs {
   RecSet view() const { return RecSet{rec.p, sc.p, seg_off.p, seg_cnt.p}; }
 };
 
+// err (optional, device int) is read back together with the stream length;
+// a non-zero value means the offsets were invalid.
 int sketch_and_lookup(const god_index* idx, const uint8_t* d_reads, SetBufs& B, uint32_t* read_flag, int via,
-                      cudaStream_t st) {
+                      const int* err, cudaStream_t st) {
   GOD_TRY(B.voff.alloc(B.n_seg + 1, st));
   GOD_TRY(exclusive_scan_u32(B.vlen.p, B.voff.p, B.n_seg, st));
   uint64_t V = 0;
+  int herr = 0;
   GOD_CK(cudaMemcpyAsync(&V, B.voff.p + B.n_seg, 8, cudaMemcpyDeviceToHost, st));
+  if (err) GOD_CK(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
   GOD_CK(cudaStreamSynchronize(st));
+  if (herr) {
+    set_error("seed: offsets must be non-decreasing and each read < 2^31 bytes");
+    return GOD_EINVAL;
+  }
   GOD_TRY(B.seg_cnt.alloc(B.n_seg, st));
   SketchJob job{};
   job.bytes = d_reads;
@@ -440,12 +548,25 @@ int sketch_and_lookup(const god_index* idx, const uint8_t* d_reads, SetBufs& B, 
   job.pat = idx->pat;
   job.seg_cnt = B.seg_cnt.p;
   job.read_flag = read_flag;
-  uint64_t total = 0;
   GOD_CK(cudaMemsetAsync(B.seg_cnt.p, 0, B.n_seg * sizeof(uint32_t), st));
-  GOD_TRY(run_sketch(job, st, B.rec, &total, nullptr));
-  B.n_rec = total;
-  GOD_TRY(B.sc.alloc(total, st));
-  GOD_TRY(lookup_keys(device_view(idx, via), &B.rec.p->key, sizeof(MinRec), total, via, B.sc.p, st));
+  StagedSketch SS;
+  GOD_TRY(run_sketch_staged(job, st, SS, nullptr));
+  B.n_rec = SS.total;
+  GOD_TRY(B.rec.alloc(SS.total, st));
+  GOD_TRY(B.sc.alloc(SS.total, st));
+  if (SS.total) {
+    const DeviceIndex di = device_view(idx, via);
+    const unsigned blocks = (unsigned)std::min<uint64_t>((SS.n_sub * 32 + kT - 1) / kT, (uint64_t)num_sms() * 16);
+    if (via == 1 && di.leaves)
+      GOD_LAUNCH(compact_lookup<1>, blocks, kT, 0, st, SS.staging.p, SS.sub_cnt.p, SS.sub_off.p, SS.n_sub, SS.WT,
+                 di, B.rec.p, B.sc.p);
+    else
+      GOD_LAUNCH(compact_lookup<0>, blocks, kT, 0, st, SS.staging.p, SS.sub_cnt.p, SS.sub_off.p, SS.n_sub, SS.WT,
+                 di, B.rec.p, B.sc.p);
+    // algorithmic bytes: record read + written (16 + 16), probe >= 32, result 8
+    prof_add_work(via == 1 && di.leaves ? "compact_lookup<1>" : "compact_lookup<0>", 72.0 * (double)SS.total,
+                  (double)SS.total);
+  }
   GOD_TRY(B.seg_off.alloc(B.n_seg + 1, st));
   GOD_TRY(exclusive_scan_u32(B.seg_cnt.p, B.seg_off.p, B.n_seg, st));
   return GOD_OK;
@@ -478,16 +599,23 @@ int seed_device(const god_index* idx, const uint8_t* d_reads, const uint64_t* d_
     if (c < cap) cap = (uint32_t)c;
   }
 
-  DBuf<int> err;
-  GOD_TRY(err.alloc(1, st));
-  GOD_CK(cudaMemsetAsync(err.p, 0, sizeof(int), st));
-  DBuf<uint32_t> need_full, shift, src, seed_seg, fb_flag, p2_flag;
+  // small per-call state: error flag + 5 list counters in one buffer
+  DBuf<unsigned long long> ctl;
+  GOD_TRY(ctl.alloc(8, st));
+  GOD_CK(cudaMemsetAsync(ctl.p, 0, 8 * sizeof(unsigned long long), st));
+  int* err = reinterpret_cast<int*>(ctl.p);
+  unsigned long long* pa_counts = ctl.p + 1;     // [fallback, seeding pass]
+  unsigned long long* fill_counts = ctl.p + 3;   // [tiny, small, large]
+  DBuf<uint32_t> need_full, shift, src, seed_seg, fb_list, p2_list;
+  DBuf<uint64_t> read_cnt, read_off;
   GOD_TRY(need_full.alloc(n, st));
   GOD_TRY(shift.alloc(n, st));
   GOD_TRY(src.alloc(n, st));
   GOD_TRY(seed_seg.alloc(n, st));
-  GOD_TRY(fb_flag.alloc(n, st));
-  GOD_TRY(p2_flag.alloc(n, st));
+  GOD_TRY(fb_list.alloc(n, st));
+  GOD_TRY(p2_list.alloc(n, st));
+  GOD_TRY(read_cnt.alloc(n, st));
+  GOD_TRY(read_off.alloc((uint64_t)n + 1, st));
   GOD_CK(cudaMemsetAsync(need_full.p, 0, n * sizeof(uint32_t), st));
 
   // ---- PA pass
@@ -495,63 +623,59 @@ int seed_device(const god_index* idx, const uint8_t* d_reads, const uint64_t* d_
   PA.n_seg = (uint64_t)n * p;
   GOD_TRY(PA.segs.alloc(PA.n_seg, st));
   GOD_TRY(PA.vlen.alloc(PA.n_seg, st));
-  GOD_LAUNCH(make_pa_segments, grid_for(n), kT, 0, st, d_offs, n, P, cap, PA.segs.p, PA.vlen.p, err.p);
-  int herr = 0;
-  GOD_CK(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
-  GOD_CK(cudaStreamSynchronize(st));
-  if (herr) {
-    set_error("seed: offsets must be non-decreasing and each read < 2^31 bytes");
-    return GOD_EINVAL;
-  }
-  GOD_TRY(sketch_and_lookup(idx, d_reads, PA, need_full.p, via, st));
+  GOD_LAUNCH(make_pa_segments, grid_for(n), kT, 0, st, d_offs, n, P, cap, PA.segs.p, PA.vlen.p, err);
+  GOD_TRY(sketch_and_lookup(idx, d_reads, PA, need_full.p, via, err, st));
   GOD_LAUNCH(pa_select, grid_for(n), kT, 0, st, n, p, t, PA.segs.p, PA.view(), need_full.p, shift.p, src.p,
-             seed_seg.p, fb_flag.p, p2_flag.p);
+             seed_seg.p, read_cnt.p, fb_list.p, p2_list.p, pa_counts);
+  unsigned long long hc[2] = {0, 0};
+  GOD_CK(cudaMemcpyAsync(hc, pa_counts, sizeof(hc), cudaMemcpyDeviceToHost, st));
+  GOD_CK(cudaStreamSynchronize(st));
+  const uint64_t n_fb = hc[0], n_p2 = hc[1];
 
   // ---- fallback: full-length pattern alignment for reads with N in the prefix
   SetBufs FB;
-  DBuf<uint32_t> fb_list;
-  uint64_t n_fb = 0;
-  GOD_TRY(compact_flags(fb_flag.p, n, fb_list, &n_fb, st));
   if (n_fb) {
     FB.n_seg = n_fb * p;
     GOD_TRY(FB.segs.alloc(FB.n_seg, st));
     GOD_TRY(FB.vlen.alloc(FB.n_seg, st));
     GOD_LAUNCH(make_list_segments, grid_for(n_fb), kT, 0, st, d_offs, fb_list.p, (uint32_t)n_fb, P, 1, shift.p,
                FB.segs.p, FB.vlen.p);
-    GOD_TRY(sketch_and_lookup(idx, d_reads, FB, nullptr, via, st));
+    GOD_TRY(sketch_and_lookup(idx, d_reads, FB, nullptr, via, nullptr, st));
     GOD_LAUNCH(pa_select_list, grid_for(n_fb), kT, 0, st, fb_list.p, (uint32_t)n_fb, p, t, FB.view(), shift.p,
-               seed_seg.p);
+               seed_seg.p, read_cnt.p);
   }
   // ---- seeding pass for reads whose shift-a segment was a prefix
   SetBufs P2;
-  DBuf<uint32_t> p2_list;
-  uint64_t n_p2 = 0;
-  GOD_TRY(compact_flags(p2_flag.p, n, p2_list, &n_p2, st));
   if (n_p2) {
     P2.n_seg = n_p2;
     GOD_TRY(P2.segs.alloc(P2.n_seg, st));
     GOD_TRY(P2.vlen.alloc(P2.n_seg, st));
     GOD_LAUNCH(make_list_segments, grid_for(n_p2), kT, 0, st, d_offs, p2_list.p, (uint32_t)n_p2, P, 0, shift.p,
                P2.segs.p, P2.vlen.p);
-    GOD_TRY(sketch_and_lookup(idx, d_reads, P2, nullptr, via, st));
+    GOD_TRY(sketch_and_lookup(idx, d_reads, P2, nullptr, via, nullptr, st));
     GOD_LAUNCH(set_seed_seg_list, grid_for(n_p2), kT, 0, st, p2_list.p, (uint32_t)n_p2, seed_seg.p);
+    GOD_LAUNCH(count_anchors_list, grid_for(n_p2 * 32), kT, 0, st, p2_list.p, (uint32_t)n_p2, P2.view(),
+               read_cnt.p);
   }
   if (o.shifts_out) {
     GOD_CK(cudaMemcpyAsync(o.shifts_out, shift.p, n * sizeof(uint32_t), cudaMemcpyDefault, st));
   }
 
-  // ---- anchors per read
+  // ---- anchors per read: offsets, length classes
   RecSets sets;
   sets.s[kSrcPA] = PA.view();
   sets.s[kSrcFB] = FB.view();
   sets.s[kSrcP2] = P2.view();
-  DBuf<uint64_t> read_cnt, read_off;
-  GOD_TRY(read_cnt.alloc(n, st));
-  GOD_TRY(read_off.alloc((uint64_t)n + 1, st));
-  GOD_LAUNCH(count_anchors, grid_for((uint64_t)n * 32), kT, 0, st, n, sets, src.p, seed_seg.p, read_cnt.p);
   GOD_TRY(exclusive_scan_u64(read_cnt.p, read_off.p, n, st));
+  DBuf<uint32_t> ltiny, lsmall, llarge;
+  GOD_TRY(ltiny.alloc(n, st));
+  GOD_TRY(lsmall.alloc(n, st));
+  GOD_TRY(llarge.alloc(n, st));
+  GOD_LAUNCH(classify_reads, grid_for(n), kT, 0, st, n, read_off.p, ltiny.p, lsmall.p, llarge.p, fill_counts);
   uint64_t total = 0;
+  unsigned long long hf[3] = {0, 0, 0};
   GOD_CK(cudaMemcpyAsync(&total, read_off.p + n, 8, cudaMemcpyDeviceToHost, st));
+  GOD_CK(cudaMemcpyAsync(hf, fill_counts, sizeof(hf), cudaMemcpyDeviceToHost, st));
   GOD_CK(cudaStreamSynchronize(st));
   *n_anchors = total;
   god_anchor* out = user_out;
@@ -564,13 +688,10 @@ int seed_device(const god_index* idx, const uint8_t* d_reads, const uint64_t* d_
   if (total == 0) return GOD_OK;
 
   // ---- fill + sort per read
-  DBuf<uint32_t> fsmall, flarge, lsmall, llarge;
-  GOD_TRY(fsmall.alloc(n, st));
-  GOD_TRY(flarge.alloc(n, st));
-  GOD_LAUNCH(classify_reads, grid_for(n), kT, 0, st, n, read_off.p, fsmall.p, flarge.p);
-  uint64_t n_small = 0, n_large = 0;
-  GOD_TRY(compact_flags(fsmall.p, n, lsmall, &n_small, st));
-  GOD_TRY(compact_flags(flarge.p, n, llarge, &n_large, st));
+  const uint64_t n_tiny = hf[0], n_small = hf[1], n_large = hf[2];
+  if (n_tiny)
+    GOD_LAUNCH(fill_sort_tiny, grid_for(n_tiny, kT, 64), kT, 0, st, sets, src.p, seed_seg.p, read_off.p, ltiny.p,
+               (uint32_t)n_tiny, idx->d_ent, out);
   if (n_small)
     GOD_LAUNCH(fill_sort_small, grid_for(n_small * 32, kT, 64), kT, 0, st, sets, src.p, seed_seg.p, read_off.p,
                lsmall.p, (uint32_t)n_small, idx->d_ent, out);

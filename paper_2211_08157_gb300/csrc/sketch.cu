@@ -582,41 +582,53 @@ SketchTune default_sketch_tune(int k, int w) {
   return SketchTune{sub_tile_for(8, k, w), 256};
 }
 
-int run_sketch(const SketchJob& job, cudaStream_t st, DBuf<MinRec>& out, uint64_t* total, const SketchTune* tune) {
+int run_sketch_staged(const SketchJob& job, cudaStream_t st, StagedSketch& o, const SketchTune* tune) {
   const SketchTune tn = clamp_tune(tune ? *tune : default_sketch_tune(job.k, job.w), job.k, job.w);
-  *total = 0;
-  if (job.V == 0) return out.alloc(0, st);
+  o.total = 0;
+  o.WT = tn.tile;
+  o.n_sub = 0;
+  if (job.V == 0) {
+    GOD_TRY(o.sub_off.alloc(1, st));
+    GOD_CK(cudaMemsetAsync(o.sub_off.p, 0, 8, st));
+    return GOD_OK;
+  }
   const int warps = tn.threads / 32;
   const uint64_t n_sub = (job.V + tn.tile - 1) / tn.tile;
   const uint64_t n_ctiles = (n_sub + warps - 1) / warps;
-  DBuf<MinRec> staging;
-  DBuf<uint32_t> sub_cnt, tseg;
-  DBuf<uint64_t> sub_off;
-  GOD_TRY(staging.alloc(n_sub * (uint64_t)tn.tile, st));
-  GOD_TRY(sub_cnt.alloc(n_sub, st));
-  GOD_TRY(sub_off.alloc(n_sub + 1, st));
+  o.n_sub = n_sub;
+  DBuf<uint32_t> tseg;
+  GOD_TRY(o.staging.alloc(n_sub * (uint64_t)tn.tile, st));
+  GOD_TRY(o.sub_cnt.alloc(n_sub, st));
+  GOD_TRY(o.sub_off.alloc(n_sub + 1, st));
   GOD_TRY(tseg.alloc(n_ctiles, st));
   SketchArgs a{};
   a.job = job;
   a.tile_seg = tseg.p;
-  a.staging = staging.p;
-  a.sub_cnt = sub_cnt.p;
+  a.staging = o.staging.p;
+  a.sub_cnt = o.sub_cnt.p;
   a.n_tiles = n_sub;
   a.T = tn.tile;
   GOD_TRY(launch_sketch<true>(a, tn, st));
-  GOD_TRY(exclusive_scan_u32(sub_cnt.p, sub_off.p, n_sub, st));
+  GOD_TRY(exclusive_scan_u32(o.sub_cnt.p, o.sub_off.p, n_sub, st));
   uint64_t tot = 0;
-  GOD_CK(cudaMemcpyAsync(&tot, sub_off.p + n_sub, 8, cudaMemcpyDeviceToHost, st));
+  GOD_CK(cudaMemcpyAsync(&tot, o.sub_off.p + n_sub, 8, cudaMemcpyDeviceToHost, st));
   GOD_CK(cudaStreamSynchronize(st));
-  *total = tot;
-  GOD_TRY(out.alloc(tot, st));
-  if (tot) {
-    const uint64_t blocks = std::min<uint64_t>((n_sub * 32 + 255) / 256, (uint64_t)num_sms() * 16);
-    GOD_LAUNCH(compact_staged, (unsigned)blocks, 256, 0, st, staging.p, sub_cnt.p, sub_off.p, n_sub, tn.tile,
-               out.p);
-  }
+  o.total = tot;
   // algorithmic bytes: every patterned base read once, every record written once
   prof_add_work("sketch", (double)(job.V - job.n_seg) + 16.0 * (double)tot, (double)(job.V - job.n_seg));
+  return GOD_OK;
+}
+
+int run_sketch(const SketchJob& job, cudaStream_t st, DBuf<MinRec>& out, uint64_t* total, const SketchTune* tune) {
+  StagedSketch S;
+  GOD_TRY(run_sketch_staged(job, st, S, tune));
+  *total = S.total;
+  GOD_TRY(out.alloc(S.total, st));
+  if (S.total) {
+    const uint64_t blocks = std::min<uint64_t>((S.n_sub * 32 + 255) / 256, (uint64_t)num_sms() * 16);
+    GOD_LAUNCH(compact_staged, (unsigned)blocks, 256, 0, st, S.staging.p, S.sub_cnt.p, S.sub_off.p, S.n_sub, S.WT,
+               out.p);
+  }
   return GOD_OK;
 }
 

@@ -37,7 +37,7 @@ def test_strerror_and_defaults():
     assert L.god_strerror(-1) == b"invalid argument"
     p = _lib.Params()
     L.god_params_init(C.byref(p))
-    assert p.pa_t == 32 and p.index_kind == 0 and p.rmi_eps_max == 64 and p.rmi_train_steps == 400
+    assert p.pa_t == 32 and p.index_kind == 0 and p.rmi_eps_max == 64 and p.rmi_train_steps == 64
     o = _lib.SeedOpts()
     L.god_seed_opts_init(C.byref(o))
     assert o.pa_t == 0xFFFFFFFF and o.via == -1
