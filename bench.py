@@ -38,6 +38,37 @@ METRIC = "read bases/sec & anchors/sec on 1 GB300, learned vs hash index, bit-ex
 L2_BYTES = 129 * 1024 * 1024
 
 
+# ALU roofline of the sketch kernel. Peak: the issue-limited 32-bit integer rate
+# from the unit counts and clock: 152 SMs x 4 schedulers x 32 lanes x 2.07 GHz.
+ALU_PEAK_TOPS = 152 * 4 * 32 * 2.07e9 / 1e12
+
+
+def sketch_ops_per_base(k: int) -> int:
+    """32-bit integer operations the method needs per patterned base (counted
+    from its arithmetic, not from the kernel): 2-bit code (4), forward and
+    reverse-complement k-mer update (14 for 64-bit codes, 7 for 32-bit),
+    canonical choice and strand (5), Wang hash (46 in 64-bit, 23 in 32-bit),
+    window minimum and maximum by van Herk / Gil-Werman (24 / 12), the
+    minimizer test (2)."""
+    if k > 16:
+        return 4 + 14 + 5 + 46 + 24 + 2
+    return 4 + 7 + 5 + 23 + (12 if k <= 15 else 24) + 2
+
+
+def recorded_traffic(kernel: str):
+    """Per-launch DRAM bytes from the committed ncu summary, if it was taken on
+    the current kernel source (source hash matches), else None."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", f"{kernel}_traffic.json")
+    src = os.path.join(ROOT, "paper_2211_08157_gb300", "csrc", "sketch.cu")
+    try:
+        d = json.load(open(path))
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        return d["bytes_per_launch"] if d.get("source_sha256") == h else None
+    except Exception:
+        return None
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -206,6 +237,77 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------- serving
+def serving_pool(ref, seed=5):
+    """Request payloads: short-read batches (1k-50k x 150 bp) and long-read batches
+    (HiFi-like and ONT-like; 10-300 reads here, the 2,000-read upper end is capped
+    to keep generation fast), each kind a third of the stream."""
+    rng = np.random.default_rng(seed)
+    pool = {"short": [], "hifi": [], "ont": []}
+    for i in range(8):
+        g = np.random.default_rng(seed * 100 + i)
+        pool["short"].append(synth.reads(ref, int(rng.integers(1000, 50001)), synth.SHORT, synth.ILLUMINA_INDEL, 0,
+                                         rng=g)[:2])
+        pool["hifi"].append(synth.reads(ref, int(rng.integers(10, 301)), synth.HIFI, synth.HIFI_ERR, 0, rng=g)[:2])
+        ont = synth.LengthModel("lognormal", mu=synth.ONT.mu, sigma=synth.ONT.sigma, lo=500, hi=30_000)
+        pool["ont"].append(synth.reads(ref, int(rng.integers(10, 301)), ont, synth.ONT_ERR, 0, rng=g)[:2])
+    return pool
+
+
+def run_serving(god, idx, pool, rate, duration, mode, slots=4, seed=11):
+    """Poisson arrivals at `rate`/s for `duration` s. mode 'server': the
+    continuous-batching server; 'plain': one god_seed call per request, FIFO."""
+    import queue
+    rng = np.random.default_rng(seed)
+    kinds = ["short", "hifi", "ont"]
+    arrivals, t = [], 0.0
+    while t < duration:
+        t += rng.exponential(1.0 / rate)
+        kind = kinds[int(rng.integers(0, 3))]
+        arrivals.append((t, pool[kind][int(rng.integers(0, len(pool[kind])))]))
+    lat, bases = [], 0
+    t0 = time.perf_counter()
+    if mode == "server":
+        srv = god.GodServer(idx, slots=slots)
+        ids = []
+
+        def waiter(q):
+            while True:
+                item = q.get()
+                if item is None:
+                    return
+                _, l = srv.wait(item, with_latency=True)
+                lat.append(l)
+
+        q = queue.Queue()
+        th = threading.Thread(target=waiter, args=(q,))
+        th.start()
+        for at, (r, o) in arrivals:
+            now = time.perf_counter() - t0
+            if at > now:
+                time.sleep(at - now)
+            q.put(srv.submit(r, o))
+            bases += int(o[-1])
+        q.put(None)
+        th.join()
+        stats = srv.stats()
+        srv.close()
+    else:
+        stats = {}
+        for at, (r, o) in arrivals:
+            now = time.perf_counter() - t0
+            if at > now:
+                time.sleep(at - now)
+            god.god_seed(idx, r, o)
+            lat.append(time.perf_counter() - t0 - at)
+            bases += int(o[-1])
+    wall = time.perf_counter() - t0
+    lat = np.array(lat)
+    return {"requests": len(arrivals), "read_bases_per_s": bases / wall, "p50_ms": float(np.percentile(lat, 50) * 1e3),
+            "p99_ms": float(np.percentile(lat, 99) * 1e3), "wall_s": wall, **({"merged_requests": stats["merged_requests"],
+            "batches": stats["batches"], "max_inflight_batches": stats["max_inflight_batches"]} if stats else {})}
+
+
 # ----------------------------------------------------------------------------- GPU arm
 def main():
     ap = argparse.ArgumentParser()
@@ -221,6 +323,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the other index kind's seed-only line")
+    ap.add_argument("--serving-seconds", type=float, default=3.0, help="0 skips the serving measurement")
+    ap.add_argument("--serving-rate", type=float, default=200.0)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gb300":
         args.warmup = 3
@@ -302,9 +406,18 @@ def main():
     hbm, peak_src = peaks()
     top = max(prof.items(), key=lambda kv: kv[1][1])
     tname, (tl, tms, tbytes, tunits) = top
-    roof = None
-    if tbytes > 0:
-        per_launch_s = (tms / tl) / 1e3
+    per_launch_s = (tms / tl) / 1e3
+    if tname == "sketch":
+        ops = sketch_ops_per_base(wl.k) * tunits / tl            # algorithmic int32 ops per launch
+        achieved = ops / per_launch_s / 1e12
+        roof = {"kernel": tname, "bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TOPS,
+                "unit": "Tops/s (int32, issue-limited)", "frac": achieved / ALU_PEAK_TOPS,
+                "traffic": recorded_traffic("sketch"), "peak_source": "derived from 152 SMs x 128 lanes x 2.07 GHz",
+                "ops_per_patterned_base": sketch_ops_per_base(wl.k), "ms_per_launch": tms / tl,
+                "hbm_view": {"achieved": (tbytes / tl) / per_launch_s / 1e9, "peak": hbm, "unit": "GB/s",
+                             "frac": (tbytes / tl) / per_launch_s / 1e9 / hbm, "peak_source": peak_src,
+                             "bytes_per_launch": tbytes / tl}}
+    elif tbytes > 0:
         achieved = (tbytes / tl) / per_launch_s / 1e9
         roof = {"kernel": tname, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "traffic": None, "peak_source": peak_src,
@@ -316,7 +429,7 @@ def main():
     sketch_roof = None
     if sk and sk[2] > 0:
         a = (sk[2] / sk[0]) / ((sk[1] / sk[0]) / 1e3) / 1e9
-        sketch_roof = {"achieved": a, "frac": a / hbm, "ms_per_step": sk[1] / args.steps,
+        sketch_roof = {"hbm_achieved_gbs": a, "hbm_frac": a / hbm, "ms_per_step": sk[1] / args.steps,
                        "patterned_bases_per_s": sk[3] / (sk[1] / 1e3)}
     kernels = {k: {"launches_per_step": v[0] / args.steps, "ms_per_step": v[1] / args.steps,
                    "share": v[1] / sum(x[1] for x in prof.values())} for k, v in
@@ -379,6 +492,22 @@ def main():
                "h2d_bytes_per_step": int(ref.nbytes + reads.nbytes + offs.nbytes),
                "d2h_bytes_per_step": int(m * 16), "ms_per_step": e2e_s * 1e3}
 
+    # ---- serving: Poisson request stream against the resident index
+    serving = None
+    if args.serving_seconds > 0 and rank == 0:
+        pool = serving_pool(ref)
+        sp = god.god_params_init(index_kind=kind, pa_t=wl.t)
+        sidx = god.god_build_index(d_ref, wl.pattern, wl.k, wl.w, wl.max_occ, params=sp)
+        run_serving(god, sidx, pool, args.serving_rate, 0.5, "server")   # warm-up
+        serving = {"index": args.index, "rate_per_s": args.serving_rate, "seconds": args.serving_seconds,
+                   "mix": "1/3 short (1k-50k x 150 bp), 1/3 HiFi-like, 1/3 ONT-like (10-300 reads), "
+                          "on the benchmark's 100 Mbp index",
+                   "continuous_batching": run_serving(god, sidx, pool, args.serving_rate, args.serving_seconds,
+                                                      "server"),
+                   "plain_one_at_a_time": run_serving(god, sidx, pool, args.serving_rate, args.serving_seconds,
+                                                      "plain")}
+        sidx.close()
+
     # ---- CPU oracle baseline (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -404,7 +533,8 @@ def main():
             "anchors_per_s": total_anchors / (ms_max / 1e3), "anchors_per_step": int(total_anchors),
             "gpu_launches": int(launches),
             "roofline": roof, "sketch_roofline": sketch_roof, "kernels": kernels,
-            "seed_only_resident_index": seed_only, "e2e": e2e, "cpu_baseline": cpu, "clocks": clk,
+            "seed_only_resident_index": seed_only, "serving": serving, "e2e": e2e, "cpu_baseline": cpu,
+            "clocks": clk,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:
