@@ -347,7 +347,7 @@ def main():
     d_offs = torch.from_numpy(offs.view(np.int64)).to(dev)
     flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device=dev)
     kind = god.GOD_INDEX_LEARNED if args.index == "learned" else god.GOD_INDEX_HASH
-    params = god.god_params_init(index_kind=kind, pa_t=wl.t)
+    params = god.god_params_init(index_kind=kind, pa_t=wl.t, tune=1)
     cap = max(int(bases // 4), 1 << 20)
     d_out = torch.empty((cap, 4), dtype=torch.int32, device=dev)
 
@@ -531,6 +531,7 @@ def main():
                        "l2": "flushed between timed steps (256 MiB write); inputs 400 MB > L2",
                        "parallelism": f"replicas x{ws}"},
             "anchors_per_s": total_anchors / (ms_max / 1e3), "anchors_per_step": int(total_anchors),
+            "autotune": god.god_autotune_report(),
             "gpu_launches": int(launches),
             "roofline": roof, "sketch_roofline": sketch_roof, "kernels": kernels,
             "seed_only_resident_index": seed_only, "serving": serving, "e2e": e2e, "cpu_baseline": cpu,

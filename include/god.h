@@ -246,6 +246,16 @@ void god_prof_enable(int on);
 void god_prof_reset(void);
 int god_prof_report(char *buf, uint64_t cap);
 
+/* The batched sketch pass is captured into a CUDA graph per (shape, stream)
+ * and replayed (on by default; calls on the legacy default stream launch
+ * directly). 0 switches graphs off process-wide. */
+void god_set_graphs(int on);
+
+/* Autotuner table: JSON list of {"k","w","p","x","len_class","threads",
+ * "chunks","ms"} entries chosen so far (god_params.tune = 1 fills it). Same
+ * return convention as god_prof_report. */
+int god_autotune_report(char *buf, uint64_t cap);
+
 /* ----------------------------------------------------------------- serving
  * A continuous-batching server over one resident index: requests (read
  * batches) are queued, admitted into free slots while device memory allows,

@@ -225,6 +225,21 @@ def god_prof_enable(on: bool = True):
     load().god_prof_enable(1 if on else 0)
 
 
+def god_set_graphs(on: bool = True):
+    load().god_set_graphs(1 if on else 0)
+
+
+def god_autotune_report() -> list:
+    """Launch shapes chosen by the sketch autotuner so far."""
+    import json
+    L = load()
+    need = L.god_autotune_report(None, 0)
+    buf = C.create_string_buffer(max(need, 2) + 64)
+    if L.god_autotune_report(buf, len(buf)) != 0:
+        raise RuntimeError("autotune report buffer too small")
+    return json.loads(buf.value.decode())
+
+
 def god_prof_reset():
     load().god_prof_reset()
 

@@ -128,6 +128,8 @@ SIGNATURES = {
     "god_prof_enable": (None, [I32]),
     "god_prof_reset": (None, []),
     "god_prof_report": (I32, [C.c_char_p, U64]),
+    "god_set_graphs": (None, [I32]),
+    "god_autotune_report": (I32, [C.c_char_p, U64]),
     "god_server_config_init": (None, [C.POINTER(ServerConfig)]),
     "god_server_create": (I32, [P_, C.POINTER(ServerConfig), C.POINTER(P_)]),
     "god_server_submit": (I32, [P_, P_, P_, U32, C.POINTER(U64)]),

@@ -17,6 +17,7 @@ namespace god {
 
 std::atomic<uint64_t> g_launches{0};
 std::atomic<int> g_prof_on{0};
+std::atomic<int> g_graphs_on{1};
 static thread_local std::string t_last_error;
 
 // ---- opt-in kernel timing
@@ -49,14 +50,24 @@ static cudaEvent_t prof_event() {
   return e;
 }
 
+// Inside stream capture the records become event-record nodes of the graph
+// (external records), so launches inside graphs are timed too.
+static void prof_record(cudaEvent_t e, cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (st && cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+    cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+  else
+    cudaEventRecord(e, st);
+}
+
 void prof_begin(cudaStream_t st, cudaEvent_t* a) {
   *a = prof_event();
-  cudaEventRecord(*a, st);
+  prof_record(*a, st);
 }
 
 void prof_end(const char* name, cudaStream_t st, cudaEvent_t a) {
   cudaEvent_t b = prof_event();
-  cudaEventRecord(b, st);
+  prof_record(b, st);
   std::lock_guard<std::mutex> lk(g_prof_mu);
   g_prof_pending.push_back(ProfPending{name, a, b});
 }
@@ -141,6 +152,48 @@ int dmalloc(void** p, size_t bytes, cudaStream_t st) {
 
 void dfree(void* p, cudaStream_t st) {
   if (p) cudaFreeAsync(p, st);
+}
+
+// ---- CUDA graphs: capture every call, update the cached executable in place
+static std::mutex g_graph_mu;
+static std::unordered_map<uint64_t, cudaGraphExec_t> g_graph_exec;
+
+int graph_run(uint64_t key, cudaStream_t st, int (*body)(void*), void* ctx) {
+  // the legacy default stream cannot be captured
+  if (!g_graphs_on.load(std::memory_order_relaxed) || st == nullptr) return body(ctx);
+  int dev = 0;
+  GOD_CK(cudaGetDevice(&dev));
+  // one executable per (shape key, stream): the same executable is never
+  // launched into two streams at once
+  key ^= ((uint64_t)(uintptr_t)st * 0x9E3779B97F4A7C15ULL) ^ ((uint64_t)dev << 56);
+  cudaGraph_t g = nullptr;
+  GOD_CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  const int rc = body(ctx);
+  const cudaError_t ec = cudaStreamEndCapture(st, &g);
+  if (rc != GOD_OK) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return rc;
+  }
+  if (ec != cudaSuccess) return cuda_fail(ec, "cudaStreamEndCapture", __FILE__, __LINE__);
+  cudaError_t e = cudaSuccess;
+  {
+    std::lock_guard<std::mutex> lk(g_graph_mu);
+    cudaGraphExec_t& ex = g_graph_exec[key];
+    if (ex) {
+      cudaGraphExecUpdateResultInfo info;
+      if (cudaGraphExecUpdate(ex, g, &info) != cudaSuccess) {
+        cudaGetLastError();
+        cudaGraphExecDestroy(ex);
+        ex = nullptr;
+      }
+    }
+    if (!ex) e = cudaGraphInstantiate(&ex, g, 0);
+    if (e == cudaSuccess) e = cudaGraphLaunch(ex, st);
+  }
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_fail(e, "graph instantiate/launch", __FILE__, __LINE__);
+  return GOD_OK;
 }
 
 bool is_device_ptr(const void* p) {
@@ -241,6 +294,8 @@ const char* god_strerror(int rc) {
 const char* god_last_error(void) { return t_last_error.c_str(); }
 
 uint64_t god_launch_count(void) { return g_launches.load(); }
+
+void god_set_graphs(int on) { g_graphs_on.store(on ? 1 : 0); }
 
 void god_prof_enable(int on) {
   if (!on) prof_collect();

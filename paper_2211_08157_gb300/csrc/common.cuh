@@ -127,8 +127,9 @@ struct __align__(16) MinRec {
 };
 
 struct SketchTune {
-  int tile;     // owned k-mer positions per tile
-  int threads;  // threads per CTA
+  int tile;     // owned k-mer positions per warp sub-tile (derived)
+  int threads;  // threads per CTA (128 or 256)
+  int chunks;   // 8-base chunks per thread per tile (1 or 2)
 };
 
 struct SketchJob {
@@ -143,6 +144,7 @@ struct SketchJob {
   uint64_t out_cap;
   uint32_t* seg_cnt;          // optional per-segment minimizer counts (zeroed by caller)
   uint32_t* read_flag;        // optional: set to 1 for reads with an N in a capped segment
+  int tune;                   // 1: pick the launch shape with the autotuner (cached per shape class)
 };
 
 // Runs the fused sparsify + 2-bit code + hash + window-minimum kernel over the
@@ -169,6 +171,19 @@ SketchTune default_sketch_tune(int k, int w);
 // Exclusive prefix sum of n values into out (n + 1 entries: out[n] = total).
 int exclusive_scan_u32(const uint32_t* in, uint64_t* out, uint64_t n, cudaStream_t st);
 int exclusive_scan_u64(const uint64_t* in, uint64_t* out, uint64_t n, cudaStream_t st);
+// The same with a caller-provided workspace of scan_ws_words(n) uint64 words
+// (no allocation: usable inside stream capture).
+uint64_t scan_ws_words(uint64_t n);
+int exclusive_scan_u32_ws(const uint32_t* in, uint64_t* out, uint64_t n, uint64_t* ws, cudaStream_t st);
+
+// ------------------------------------------------------------------ graphs
+// Runs `body` (a fixed sequence of kernel launches on st, no allocation, no
+// host synchronisation) as a CUDA graph: it is captured on every call and the
+// executable graph cached under `key` is updated in place (cudaGraphExecUpdate)
+// and launched; a topology change re-instantiates it. Direct launches when
+// graphs are switched off.
+int graph_run(uint64_t key, cudaStream_t st, int (*body)(void*), void* ctx);
+extern std::atomic<int> g_graphs_on;
 
 // ------------------------------------------------------------------ radix sort
 // Stable LSD radix sort of (key, value) pairs by bits [0, key_bits) of the key.

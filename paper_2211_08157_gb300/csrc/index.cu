@@ -162,6 +162,7 @@ int build_index_device(god_index* idx, const uint8_t* d_ref, uint64_t len, cudaS
   job.k = idx->k;
   job.w = idx->w;
   job.pat = P;
+  job.tune = idx->params.tune;
   DBuf<MinRec> rec;
   uint64_t total = 0;
   GOD_TRY(run_sketch(job, st, rec, &total, nullptr));

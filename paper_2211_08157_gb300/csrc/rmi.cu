@@ -225,12 +225,6 @@ __global__ void leaf_bounds(const uint64_t* leaf_sorted, uint64_t U, uint32_t* l
   }
 }
 
-__device__ __forceinline__ double warp_sum_d(double v) {
-#pragma unroll
-  for (int d = 16; d >= 1; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
-  return v;
-}
-
 // One thread per leaf: least squares in double over the leaf's keys (ranks
 // ascend inside the run, so the first key is the smallest = base), then the
 // error bound with the FP32 prediction of the lookup path.

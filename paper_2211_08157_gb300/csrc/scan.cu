@@ -90,24 +90,34 @@ __global__ void __launch_bounds__(kScanThreads) tile_scan_kernel(const T* in, ui
 }
 
 template <typename T>
-int scan_impl(const T* in, uint64_t* out, uint64_t n, cudaStream_t st) {
+int scan_launch(const T* in, uint64_t* out, uint64_t n, uint64_t* sums, cudaStream_t st) {
   if (n == 0) {
     GOD_CK(cudaMemsetAsync(out, 0, sizeof(uint64_t), st));
     return GOD_OK;
   }
   const uint64_t nt = (n + kScanTile - 1) / kScanTile;
-  DBuf<uint64_t> sums;
-  GOD_TRY(sums.alloc(nt + 1, st));
-  GOD_LAUNCH(tile_sums_kernel<T>, (unsigned)nt, kScanThreads, 0, st, in, n, sums.p);
-  GOD_LAUNCH(scan_sums_kernel, 1, kScanThreads, 0, st, sums.p, nt);
-  GOD_LAUNCH(tile_scan_kernel<T>, (unsigned)nt, kScanThreads, 0, st, in, n, sums.p, out, nt);
+  GOD_LAUNCH(tile_sums_kernel<T>, (unsigned)nt, kScanThreads, 0, st, in, n, sums);
+  GOD_LAUNCH(scan_sums_kernel, 1, kScanThreads, 0, st, sums, nt);
+  GOD_LAUNCH(tile_scan_kernel<T>, (unsigned)nt, kScanThreads, 0, st, in, n, sums, out, nt);
   return GOD_OK;
+}
+
+template <typename T>
+int scan_impl(const T* in, uint64_t* out, uint64_t n, cudaStream_t st) {
+  DBuf<uint64_t> sums;
+  GOD_TRY(sums.alloc(scan_ws_words(n), st));
+  return scan_launch(in, out, n, sums.p, st);
 }
 
 }  // namespace
 
+uint64_t scan_ws_words(uint64_t n) { return (n + kScanTile - 1) / kScanTile + 1; }
+
 int exclusive_scan_u32(const uint32_t* in, uint64_t* out, uint64_t n, cudaStream_t st) {
   return scan_impl(in, out, n, st);
+}
+int exclusive_scan_u32_ws(const uint32_t* in, uint64_t* out, uint64_t n, uint64_t* ws, cudaStream_t st) {
+  return scan_launch(in, out, n, ws, st);
 }
 int exclusive_scan_u64(const uint64_t* in, uint64_t* out, uint64_t n, cudaStream_t st) {
   return scan_impl(in, out, n, st);

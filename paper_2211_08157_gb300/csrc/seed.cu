@@ -548,7 +548,7 @@ int sketch_and_lookup(const god_index* idx, const uint8_t* d_reads, SetBufs& B, 
   job.pat = idx->pat;
   job.seg_cnt = B.seg_cnt.p;
   job.read_flag = read_flag;
-  GOD_CK(cudaMemsetAsync(B.seg_cnt.p, 0, B.n_seg * sizeof(uint32_t), st));
+  job.tune = idx->params.tune;
   StagedSketch SS;
   GOD_TRY(run_sketch_staged(job, st, SS, nullptr));
   B.n_rec = SS.total;

@@ -27,7 +27,13 @@
 //  5. ordered compaction with a decoupled look-back over tile tickets, so the
 //     output is in stream order (segment, position) with no second pass.
 #include <algorithm>
+#include <map>
 #include <mutex>
+#include <tuple>
+
+#include <cstdio>
+#include <cstring>
+#include <string>
 
 #include "common.cuh"
 
@@ -38,7 +44,6 @@ constexpr uint64_t kFlagAgg = 1ULL << 62;
 constexpr uint64_t kFlagIncl = 2ULL << 62;
 constexpr uint64_t kValMask = (1ULL << 62) - 1;
 constexpr uint32_t kSpinLimit = 1u << 22;   // ~0.1-1 s of polling before giving up
-constexpr uint64_t kPalin = ~0ULL;
 
 __device__ __forceinline__ uint32_t base_code(uint8_t b) {
   const uint32_t c = b & 0xDFu;  // upper-case letters; other bytes stay non-ACGT
@@ -112,10 +117,10 @@ __device__ __forceinline__ KT palin_mark() { return (KT)~(KT)0; }
 
 constexpr int kBndCache = 256;  // segment boundaries cached per tile
 
-// Owned positions per warp sub-tile: as many as let one 8-base chunk per
+// Owned positions per warp sub-tile: as many as let `chunks` 8-base chunks per
 // thread cover the CTA tile plus its halo (multiple of 8, at least 64).
-__host__ __device__ inline int sub_tile_for(int warps, int k, int w) {
-  int wt = (8 * 32 * warps - 2 * (w - 1) - (k - 1)) / warps;
+__host__ __device__ inline int sub_tile_for(int warps, int k, int w, int chunks = 1) {
+  int wt = (8 * chunks * 32 * warps - 2 * (w - 1) - (k - 1)) / warps;
   wt &= ~7;
   return wt < 64 ? 64 : wt;
 }
@@ -572,18 +577,141 @@ __global__ void compact_staged(const MinRec* __restrict__ staging, const uint32_
 
 SketchTune clamp_tune(SketchTune tn, int k, int w) {
   if (tn.threads != 128 && tn.threads != 256) tn.threads = 256;
-  tn.tile = sub_tile_for(tn.threads / 32, k, w);
+  if (tn.chunks != 1 && tn.chunks != 2) tn.chunks = 1;
+  const int kt = k <= 15 ? 4 : 8;
+  // shrink until the tile workspace fits one CTA's shared memory
+  while (true) {
+    tn.tile = sub_tile_for(tn.threads / 32, k, w, tn.chunks);
+    if (tile_layout(tn.threads / 32, tn.tile, k, w, kt).bytes + 4096 <= 227 * 1024 || tn.chunks == 1) break;
+    tn.chunks = 1;
+  }
   return tn;
+}
+
+// ---- autotuner: launch shape per (k, w, pattern, mean segment length class)
+struct TuneEntry {
+  SketchTune tn;
+  float ms;
+};
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int, int, int>, TuneEntry> g_tune;
+
+int len_class(const SketchJob& job) {
+  const uint64_t mean = job.n_seg ? job.V / job.n_seg : job.V;
+  int c = 0;
+  while ((1ull << (c + 1)) <= mean && c < 40) ++c;
+  return c;
 }
 
 }  // namespace
 
 SketchTune default_sketch_tune(int k, int w) {
-  return SketchTune{sub_tile_for(8, k, w), 256};
+  return SketchTune{sub_tile_for(8, k, w), 256, 1};
 }
 
+namespace {
+struct SketchGraphCtx {
+  SketchArgs a;
+  SketchTune tn;
+  uint64_t* scan_ws;
+  uint64_t* sub_off;
+  cudaStream_t st;
+};
+// The persistent sketch pass as one launch sequence: per-tile first segments,
+// the sketch kernel, and the scan of the sub-tile counts.
+int sketch_pass(void* p) {
+  SketchGraphCtx* c = static_cast<SketchGraphCtx*>(p);
+  GOD_TRY(launch_sketch<true>(c->a, c->tn, c->st));
+  GOD_TRY(exclusive_scan_u32_ws(c->a.sub_cnt, c->sub_off, c->a.n_tiles, c->scan_ws, c->st));
+  return GOD_OK;
+}
+
+// Staging buffers for one launch shape, allocated before any capture.
+struct StageBufs {
+  DBuf<uint32_t> tseg;
+  DBuf<uint64_t> scan_ws;
+};
+
+int prepare(const SketchJob& job, const SketchTune& tn, cudaStream_t st, StagedSketch& o, StageBufs& b,
+            SketchGraphCtx& c) {
+  const int warps = tn.threads / 32;
+  const uint64_t n_sub = (job.V + tn.tile - 1) / tn.tile;
+  const uint64_t n_ctiles = (n_sub + warps - 1) / warps;
+  o.n_sub = n_sub;
+  o.WT = tn.tile;
+  GOD_TRY(o.staging.alloc(n_sub * (uint64_t)tn.tile, st));
+  GOD_TRY(o.sub_cnt.alloc(n_sub, st));
+  GOD_TRY(o.sub_off.alloc(n_sub + 1, st));
+  GOD_TRY(b.tseg.alloc(n_ctiles, st));
+  GOD_TRY(b.scan_ws.alloc(scan_ws_words(n_sub), st));
+  c.a = SketchArgs{};
+  c.a.job = job;
+  c.a.tile_seg = b.tseg.p;
+  c.a.staging = o.staging.p;
+  c.a.sub_cnt = o.sub_cnt.p;
+  c.a.n_tiles = n_sub;
+  c.a.T = tn.tile;
+  c.tn = tn;
+  c.scan_ws = b.scan_ws.p;
+  c.sub_off = o.sub_off.p;
+  c.st = st;
+  return GOD_OK;
+}
+
+// Times each candidate launch shape once on this job (direct launches) and
+// returns the fastest; the choice is cached per shape class.
+int autotune(const SketchJob& job, cudaStream_t st, SketchTune* best) {
+  int dev = 0;
+  GOD_CK(cudaGetDevice(&dev));
+  const auto key = std::make_tuple(dev, job.k, job.w, job.pat.p * 64 + job.pat.x, len_class(job), (int)(job.seg_cnt != nullptr));
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      *best = it->second.tn;
+      return GOD_OK;
+    }
+  }
+  const SketchTune cands[4] = {{0, 256, 1}, {0, 128, 1}, {0, 256, 2}, {0, 128, 2}};
+  float best_ms = 1e30f;
+  SketchTune pick = default_sketch_tune(job.k, job.w);
+  cudaEvent_t e0, e1;
+  GOD_CK(cudaEventCreate(&e0));
+  GOD_CK(cudaEventCreate(&e1));
+  for (const SketchTune& cand : cands) {
+    const SketchTune tn = clamp_tune(cand, job.k, job.w);
+    StagedSketch o;
+    StageBufs b;
+    SketchGraphCtx c;
+    int rc = prepare(job, tn, st, o, b, c);
+    if (rc == GOD_OK && job.seg_cnt) rc = cudaMemsetAsync(job.seg_cnt, 0, (size_t)job.n_seg * 4, st) ? GOD_ECUDA : GOD_OK;
+    if (rc == GOD_OK) rc = cudaEventRecord(e0, st) ? GOD_ECUDA : GOD_OK;
+    if (rc == GOD_OK) rc = sketch_pass(&c);
+    if (rc == GOD_OK) rc = cudaEventRecord(e1, st) ? GOD_ECUDA : GOD_OK;
+    float ms = 1e30f;
+    if (rc == GOD_OK) rc = cudaEventSynchronize(e1) ? GOD_ECUDA : GOD_OK;
+    if (rc == GOD_OK) rc = cudaEventElapsedTime(&ms, e0, e1) ? GOD_ECUDA : GOD_OK;
+    if (rc != GOD_OK) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return rc == GOD_ECUDA ? cuda_fail(cudaGetLastError(), "autotune", __FILE__, __LINE__) : rc;
+    }
+    if (ms < best_ms) {
+      best_ms = ms;
+      pick = tn;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[key] = TuneEntry{pick, best_ms};
+  *best = pick;
+  return GOD_OK;
+}
+}  // namespace
+
 int run_sketch_staged(const SketchJob& job, cudaStream_t st, StagedSketch& o, const SketchTune* tune) {
-  const SketchTune tn = clamp_tune(tune ? *tune : default_sketch_tune(job.k, job.w), job.k, job.w);
+  SketchTune tn = clamp_tune(tune ? *tune : default_sketch_tune(job.k, job.w), job.k, job.w);
   o.total = 0;
   o.WT = tn.tile;
   o.n_sub = 0;
@@ -592,26 +720,16 @@ int run_sketch_staged(const SketchJob& job, cudaStream_t st, StagedSketch& o, co
     GOD_CK(cudaMemsetAsync(o.sub_off.p, 0, 8, st));
     return GOD_OK;
   }
-  const int warps = tn.threads / 32;
-  const uint64_t n_sub = (job.V + tn.tile - 1) / tn.tile;
-  const uint64_t n_ctiles = (n_sub + warps - 1) / warps;
-  o.n_sub = n_sub;
-  DBuf<uint32_t> tseg;
-  GOD_TRY(o.staging.alloc(n_sub * (uint64_t)tn.tile, st));
-  GOD_TRY(o.sub_cnt.alloc(n_sub, st));
-  GOD_TRY(o.sub_off.alloc(n_sub + 1, st));
-  GOD_TRY(tseg.alloc(n_ctiles, st));
-  SketchArgs a{};
-  a.job = job;
-  a.tile_seg = tseg.p;
-  a.staging = o.staging.p;
-  a.sub_cnt = o.sub_cnt.p;
-  a.n_tiles = n_sub;
-  a.T = tn.tile;
-  GOD_TRY(launch_sketch<true>(a, tn, st));
-  GOD_TRY(exclusive_scan_u32(o.sub_cnt.p, o.sub_off.p, n_sub, st));
+  if (job.tune && !tune) GOD_TRY(autotune(job, st, &tn));
+  StageBufs b;
+  SketchGraphCtx c;
+  GOD_TRY(prepare(job, tn, st, o, b, c));
+  if (job.seg_cnt) GOD_CK(cudaMemsetAsync(job.seg_cnt, 0, (size_t)job.n_seg * 4, st));
+  const uint64_t key = ((uint64_t)job.k << 48) ^ ((uint64_t)tn.threads << 36) ^ ((uint64_t)tn.chunks << 32) ^
+                       ((uint64_t)(job.seg_cnt != nullptr) << 31) ^ (uint64_t)(job.read_flag != nullptr) ^ 0x5ca1ab1eULL;
+  GOD_TRY(graph_run(key, st, sketch_pass, &c));
   uint64_t tot = 0;
-  GOD_CK(cudaMemcpyAsync(&tot, o.sub_off.p + n_sub, 8, cudaMemcpyDeviceToHost, st));
+  GOD_CK(cudaMemcpyAsync(&tot, o.sub_off.p + o.n_sub, 8, cudaMemcpyDeviceToHost, st));
   GOD_CK(cudaStreamSynchronize(st));
   o.total = tot;
   // algorithmic bytes: every patterned base read once, every record written once
@@ -761,4 +879,28 @@ extern "C" int god_sketch_noalloc(const uint8_t* d_seq, uint64_t len, const char
     return GOD_ETIMEOUT;
   }
   return host[0] > cap ? GOD_ERANGE : GOD_OK;
+}
+
+extern "C" int god_autotune_report(char* buf, uint64_t cap) {
+  using namespace god;
+  std::string out = "[";
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    bool first = true;
+    for (auto& kv : g_tune) {
+      char item[256];
+      snprintf(item, sizeof item,
+               "%s{\"device\": %d, \"k\": %d, \"w\": %d, \"p\": %d, \"x\": %d, \"len_class\": %d, "
+               "\"segment_counts\": %d, \"threads\": %d, \"chunks\": %d, \"tile\": %d, \"ms\": %.4f}",
+               first ? "" : ", ", std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first),
+               std::get<3>(kv.first) / 64, std::get<3>(kv.first) % 64, std::get<4>(kv.first), std::get<5>(kv.first),
+               kv.second.tn.threads, kv.second.tn.chunks, kv.second.tn.tile, kv.second.ms);
+      out += item;
+      first = false;
+    }
+  }
+  out += "]";
+  if (!buf || cap < out.size() + 1) return (int)(out.size() + 1);
+  memcpy(buf, out.c_str(), out.size() + 1);
+  return 0;
 }
