@@ -262,12 +262,16 @@ static void free_index(god_index* idx) {
   int prev = 0;
   cudaGetDevice(&prev);
   cudaSetDevice(idx->device);
-  cudaFree(idx->d_keys);
-  cudaFree(idx->d_start);
+  if (idx->d_arena) {
+    cudaFree(idx->d_arena);  // keys, offsets and leaves live in the arena
+  } else {
+    cudaFree(idx->d_keys);
+    cudaFree(idx->d_start);
+    cudaFree(idx->d_leaves);
+  }
   cudaFree(idx->d_ent);
   cudaFree(idx->d_ht);
   cudaFree(idx->d_root);
-  cudaFree(idx->d_leaves);
   cudaSetDevice(prev);
   delete idx;
 }

@@ -248,6 +248,9 @@ struct god_index {
   double rmi_mean_eps, rmi_fallback_key_frac;
   float rmi_loss;
   uint64_t device_bytes;
+  // learned index: keys, offsets and leaves in one allocation
+  void* d_arena;
+  size_t arena_bytes;
 };
 
 namespace god {

@@ -478,7 +478,26 @@ int build_rmi(god_index* idx, cudaStream_t st) {
   GOD_CK(cudaStreamSynchronize(st));
   idx->root = R;
   idx->d_root = d_root.take();
-  idx->d_leaves = leaves.take();
+  // one arena [keys | offsets | leaves]: the structure a learned lookup touches
+  {
+    const size_t kb = ((U * 8) + 255) & ~(size_t)255;
+    const size_t sb = (((U + 1) * 4) + 255) & ~(size_t)255;
+    const size_t lb = (size_t)n_leaves * sizeof(RmiLeaf);
+    void* arena = nullptr;
+    GOD_TRY(dmalloc(&arena, kb + sb + lb, st));
+    char* a8 = static_cast<char*>(arena);
+    GOD_CK(cudaMemcpyAsync(a8, idx->d_keys, U * 8, cudaMemcpyDeviceToDevice, st));
+    GOD_CK(cudaMemcpyAsync(a8 + kb, idx->d_start, (U + 1) * 4, cudaMemcpyDeviceToDevice, st));
+    GOD_CK(cudaMemcpyAsync(a8 + kb + sb, leaves.p, lb, cudaMemcpyDeviceToDevice, st));
+    GOD_CK(cudaStreamSynchronize(st));
+    dfree(idx->d_keys, st);
+    dfree(idx->d_start, st);
+    idx->d_keys = reinterpret_cast<uint64_t*>(a8);
+    idx->d_start = reinterpret_cast<uint32_t*>(a8 + kb);
+    idx->d_leaves = reinterpret_cast<RmiLeaf*>(a8 + kb + sb);
+    idx->d_arena = arena;
+    idx->arena_bytes = kb + sb + lb;
+  }
   idx->has_rmi = 1;
   idx->rmi_mean_eps = (double)hs[0] / (double)U;
   idx->rmi_fallback_leaves = (uint32_t)hs[3];
