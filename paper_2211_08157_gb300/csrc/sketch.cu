@@ -50,32 +50,72 @@ __device__ __forceinline__ uint32_t base_code(uint8_t b) {
   return c == 'A' ? 0u : c == 'C' ? 1u : c == 'G' ? 2u : c == 'T' ? 3u : 4u;
 }
 
-// Wang's 64-bit integer hash restricted to 2k bits, written in shift-add form.
-// For 2k <= 32 the same steps in 32-bit arithmetic give the identical value.
+// (x * c + a) mod 2^64 from two 32-bit multiply-adds.
+__device__ __forceinline__ uint64_t mad_c64(uint64_t x, uint32_t c, uint64_t a) {
+  uint64_t lo;
+  uint32_t hi;
+  asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(lo) : "r"((uint32_t)x), "r"(c), "l"(a));
+  asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(hi) : "r"((uint32_t)(x >> 32)), "r"(c), "r"((uint32_t)(lo >> 32)));
+  return ((uint64_t)hi << 32) | (uint32_t)lo;
+}
+
+// x ^ (x >> S) for 0 < S < 32, on the two 32-bit halves.
+template <int S>
+__device__ __forceinline__ uint64_t xorshr64(uint64_t x) {
+  const uint32_t lo = (uint32_t)x, hi = (uint32_t)(x >> 32);
+  return ((uint64_t)(hi ^ (hi >> S)) << 32) | (lo ^ __funnelshift_r(lo, hi, S));
+}
+
+// Wang's 64-bit integer hash restricted to 2k bits. Its shift-add steps are
+// multiplications by constants: ~x + (x << 21) = x * (2^21 - 1) - 1,
+// x + (x << 3) + (x << 8) = 265 x, x + (x << 2) + (x << 4) = 21 x and
+// x + (x << 31) = (2^31 + 1) x (mod 2^64), so each is one 64 x 32-bit
+// multiply-add. WIDE (2k > 32): the mask only touches the high half. Otherwise
+// the same steps in 32-bit arithmetic give the identical value.
 template <bool WIDE>
 __device__ __forceinline__ uint64_t wang_mix(uint64_t key, uint64_t mask) {
   if (WIDE) {
     uint64_t x = key;
-    x = (~x + (x << 21)) & mask;
-    x = x ^ (x >> 24);
-    x = ((x + (x << 3)) + (x << 8)) & mask;
-    x = x ^ (x >> 14);
-    x = ((x + (x << 2)) + (x << 4)) & mask;
-    x = x ^ (x >> 28);
-    x = (x + (x << 31)) & mask;
+    x = mad_c64(x, 0x1FFFFFu, ~0ULL) & mask;
+    x = xorshr64<24>(x);
+    x = mad_c64(x, 265u, 0) & mask;
+    x = xorshr64<14>(x);
+    x = mad_c64(x, 21u, 0) & mask;
+    x = xorshr64<28>(x);
+    x = mad_c64(x, 0x80000001u, 0) & mask;
     return x;
   } else {
     uint32_t x = (uint32_t)key;
     const uint32_t m = (uint32_t)mask;
-    x = (~x + (x << 21)) & m;
+    x = (x * 0x1FFFFFu + 0xFFFFFFFFu) & m;
     x = x ^ (x >> 24);
-    x = ((x + (x << 3)) + (x << 8)) & m;
+    x = (x * 265u) & m;
     x = x ^ (x >> 14);
-    x = ((x + (x << 2)) + (x << 4)) & m;
+    x = (x * 21u) & m;
     x = x ^ (x >> 28);
-    x = (x + (x << 31)) & m;
+    x = (x * 0x80000001u) & m;
     return x;
   }
+}
+
+// q = j / x, r = j mod x with xinv = floor((2^32 - 1) / x): the estimate
+// umulhi(j, xinv) is q or q - 1 for every j < 2^32, so one correction step.
+__device__ __forceinline__ void divmod_x(uint32_t j, uint32_t x, uint32_t xinv, uint32_t& q, uint32_t& r) {
+  q = __umulhi(j, xinv);
+  r = j - q * x;
+  if (r >= x) {
+    r -= x;
+    ++q;
+  }
+}
+
+// Reverses the order of the 32 two-bit fields of v (field i of the big-endian
+// word becomes field i from the bottom, bit order inside a field kept).
+__device__ __forceinline__ uint64_t rev_pairs64(uint64_t v) {
+  const uint32_t lo = __brev((uint32_t)(v >> 32)), hi = __brev((uint32_t)v);
+  const uint32_t lo2 = ((lo >> 1) & 0x55555555u) | ((lo & 0x55555555u) << 1);
+  const uint32_t hi2 = ((hi >> 1) & 0x55555555u) | ((hi & 0x55555555u) << 1);
+  return ((uint64_t)hi2 << 32) | lo2;
 }
 
 __device__ __forceinline__ uint64_t ld_acquire_u64(const unsigned long long* p) {
@@ -125,14 +165,18 @@ __host__ __device__ inline int sub_tile_for(int warps, int k, int w, int chunks 
   return wt < 64 ? 64 : wt;
 }
 
+// Window stage of the kernel: blocks of up to MW keys in registers (MW = 12
+// or 20), or shared-memory passes for any w (MW = 0).
+__host__ __device__ inline int window_mw(int w) { return w <= 12 ? 12 : w <= 20 ? 20 : 0; }
+
 // Shared-memory layout of one CTA tile of T = WARPS * WT owned positions
 // (host and device agree on it).
 struct TileLayout {
-  int n_keys, n_codes, n_groups, n_chunks, n_win_w;
-  size_t off_sm, off_f, off_c, off_cst, off_nm, off_zb, off_sel, off_list, bytes;
+  int n_keys, n_codes, n_groups, n_chunks, n_win_w, warp_scr;
+  size_t off_sm, off_f, off_c, off_cst, off_nm, off_vb, off_zb, off_sel, off_list, bytes;
 };
 
-__host__ __device__ inline TileLayout tile_layout(int warps, int WT, int k, int w, int kt) {
+__host__ __device__ inline TileLayout tile_layout(int warps, int WT, int k, int w, int kt, int mw) {
   TileLayout L;
   const int T = warps * WT;
   L.n_keys = T + 2 * (w - 1);            // k-mer positions [A - w + 1, A + T + w - 1)
@@ -141,9 +185,11 @@ __host__ __device__ inline TileLayout tile_layout(int warps, int WT, int k, int 
   L.n_chunks = L.n_groups * 4;           // 8-base chunks
   L.n_win_w = WT + w - 1;                // windows a warp evaluates
   const int n_keys_w = WT + 2 * (w - 1);
+  // per warp: window minima, one column per lane (MW > 0), or S/M and SX
+  L.warp_scr = mw > 0 ? mw * 32 : 2 * n_keys_w;
   size_t o = ((size_t)L.n_keys * kt + 15) & ~(size_t)15;        // K (whole tile)
   L.off_sm = o;
-  o += (((size_t)2 * n_keys_w * kt) * warps + 15) & ~(size_t)15;  // per warp: S/M, SX
+  o += (((size_t)L.warp_scr * kt) * warps + 15) & ~(size_t)15;
   L.off_f = o;
   o += (size_t)(L.n_groups + 1) * 8;
   L.off_c = o;
@@ -152,10 +198,12 @@ __host__ __device__ inline TileLayout tile_layout(int warps, int WT, int k, int 
   o += (size_t)L.n_chunks * 8;
   L.off_nm = o;
   o += (size_t)(L.n_groups + 1) * 4;
+  L.off_vb = o;
+  o += (size_t)(L.n_keys / 32 + 3) * 4;  // usable-key bits (key not 0 and not the palindrome mark)
   L.off_zb = o;
   o += (size_t)L.n_keys;
   L.off_sel = o;
-  o += (size_t)T;                        // selection flags
+  o += mw > 0 ? 0 : (size_t)T;           // selection flags (shared-memory window stage)
   o = (o + 3) & ~(size_t)3;
   L.off_list = o;
   o += (size_t)T * 2;                    // per warp: selected positions (u16)
@@ -191,6 +239,189 @@ __device__ __forceinline__ uint64_t take64_le(uint64_t w0, uint64_t w1, uint32_t
   return ((uint64_t)hi << 32) | lo;
 }
 
+// Window stage with blocks of w <= MW keys in registers (van Herk /
+// Gil-Werman): in a pass, lane b takes block b (keys [b w, b w + w) of the
+// warp's sub-tile). Its suffix minima stay in registers and the prefix minima
+// of block b + 1 come from lane b + 1 by shuffle, giving the window minima that
+// start in block b (kept in the lane's own shared-memory column); the same two
+// sweeps over those minima give the largest window minimum covering each
+// position. Lane b reads keys of blocks b .. b + 2, so a pass completes the
+// blocks of lanes 0..29; lanes past the last needed block repeat it. Only the
+// windows covering owned positions decide the result, and those lie inside the
+// sub-tile's keys, so the reads past its end (still inside the tile's shared
+// memory) need no guard. Vb holds the tile's usable-key bits. Appends the
+// selected owned positions to `list` in order and returns their number.
+template <int MW, typename KT>
+__device__ __forceinline__ uint32_t window_select_reg(const KT* __restrict__ Kw, KT* __restrict__ col,
+                                                      const uint32_t* __restrict__ Vb, int wo, int w, int WT,
+                                                      int lane, uint16_t* __restrict__ list) {
+  const unsigned FULL = 0xffffffffu;
+  uint32_t cnt = 0;
+  const int nb_out = (WT + w - 1) / w;       // blocks holding owned positions
+  for (int gb = 0; gb < nb_out; gb += 30) {
+    const int s = min(gb + lane, nb_out + 1) * w;
+    KT r[MW];
+    KT m = palin_mark<KT>();
+#pragma unroll
+    for (int t = MW - 1; t >= 0; --t) {      // suffix minima of the block
+      if (t < w) {
+        m = min(m, Kw[s + t]);
+        r[t] = m;
+      }
+    }
+    KT pm = palin_mark<KT>();
+#pragma unroll
+    for (int t = 0; t < MW; ++t) {           // minimum of the window starting at s + t
+      if (t < w) {
+        KT mv = r[t];
+        if (t > 0) mv = min(mv, (KT)__shfl_down_sync(FULL, pm, 1));
+        col[t * 32 + lane] = mv;
+        pm = min(pm, Kw[s + t]);
+      }
+    }
+    KT mx = 0;
+#pragma unroll
+    for (int t = MW - 1; t >= 0; --t) {      // suffix maxima of the window minima
+      if (t < w) {
+        mx = max(mx, col[t * 32 + lane]);
+        r[t] = mx;
+      }
+    }
+    KT px = 0;
+    uint32_t fl = 0;
+#pragma unroll
+    for (int t = 0; t < MW; ++t) {           // largest minimum covering s + t, equal to its key?
+      if (t < w) {
+        KT cover = r[t];
+        if (t > 0) cover = max(cover, (KT)__shfl_down_sync(FULL, px, 1));
+        if (Kw[s + t + w - 1] == cover) fl |= 1u << t;
+        px = max(px, col[t * 32 + lane]);
+      }
+    }
+    // usable keys at s + w - 1 .. s + 2w - 2, owned positions only, lanes 0..29
+    const int u0 = wo + s + w - 1;
+    fl &= __funnelshift_r(Vb[u0 >> 5], Vb[(u0 >> 5) + 1], u0 & 31);
+    const int own = WT - s;
+    if (own < 32) fl &= own > 0 ? (1u << own) - 1u : 0u;
+    if (lane >= 30 || gb + lane >= nb_out) fl = 0;
+    const uint32_t c = __popc(fl);
+    uint32_t inc = c;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t y = __shfl_up_sync(FULL, inc, d);
+      if (lane >= d) inc += y;
+    }
+    uint32_t at = cnt + inc - c;
+    while (fl) {
+      list[at++] = (uint16_t)(s + __ffs(fl) - 1);
+      fl &= fl - 1;
+    }
+    cnt += __shfl_sync(FULL, inc, 31);
+  }
+  __syncwarp();
+  return cnt;
+}
+
+// Window stage for any w: the same van Herk / Gil-Werman sweeps with both
+// extrema arrays in shared memory (S/M and SX), selection flags, compaction.
+template <typename KT>
+__device__ __forceinline__ uint32_t window_select_smem(const KT* __restrict__ Kw, KT* SM, KT* SX, uint8_t* sel,
+                                                       int w, int n_keys_w, int n_win_w, int WT, int lane,
+                                                       uint16_t* __restrict__ list) {
+  const KT PALIN = palin_mark<KT>();
+  const unsigned FULL = 0xffffffffu;
+  {
+    const int nb = (n_keys_w + w - 1) / w;
+    for (int gb = 0; gb < nb; gb += 31) {
+      const int b = gb + lane;
+      const int s = b * w;
+      const bool live = b < nb;
+      KT m = PALIN;
+      for (int t = w - 1; t >= 0; --t) {
+        const int i = s + t;
+        if (live && i < n_keys_w) { m = min(m, Kw[i]); SM[i] = m; }
+      }
+      __syncwarp();
+      KT pm = PALIN;
+      for (int t = 0; t < w; ++t) {
+        const int i = s + t;
+        const KT kv = (live && i < n_keys_w) ? Kw[i] : PALIN;
+        const KT nxt = __shfl_down_sync(FULL, pm, 1);   // next block's prefix over offsets < t
+        if (lane < 31 && live && i < n_win_w && t) SM[i] = min(SM[i], nxt);
+        pm = min(pm, kv);
+      }
+      __syncwarp();
+    }
+  }
+  {
+    const int nb = (n_win_w + w - 1) / w;
+    for (int gb = 0; gb < nb; gb += 31) {
+      const int b = gb + lane;
+      const int s = b * w;
+      const bool live = b < nb;
+      KT m = 0;
+      for (int t = w - 1; t >= 0; --t) {
+        const int i = s + t;
+        if (live && i < n_win_w) { m = max(m, SM[i]); SX[i] = m; }
+      }
+      __syncwarp();
+      KT px = 0;
+      for (int t = 0; t < w; ++t) {
+        const int i = s + t;
+        const KT mv = (live && i < n_win_w) ? SM[i] : (KT)0;
+        const KT nxt = __shfl_down_sync(FULL, px, 1);
+        if (lane < 31 && live && i < WT) {
+          const KT mx = t == 0 ? SX[i] : max(SX[i], nxt);
+          const KT kk = Kw[i + w - 1];
+          sel[i] = (kk != 0 && kk != PALIN && kk == mx) ? 1 : 0;
+        }
+        px = max(px, mv);
+      }
+      __syncwarp();
+    }
+  }
+  const unsigned lt = (1u << lane) - 1u;
+  uint32_t cnt = 0;
+  for (int o0 = 0; o0 < WT; o0 += 32) {
+    const bool f = o0 + lane < WT && sel[o0 + lane] != 0;
+    const unsigned bal = __ballot_sync(FULL, f);
+    if (f) list[cnt + __popc(bal & lt)] = (uint16_t)(o0 + lane);
+    cnt += __popc(bal);
+  }
+  __syncwarp();
+  return cnt;
+}
+
+// Record of the minimizer at tile k-mer index u: its segment from the chunk
+// state (walking over segment ends), then the closed-form original position.
+template <typename KT>
+__device__ __forceinline__ MinRec make_record(const SketchJob& J, const int2* cst, const KT* K, const uint8_t* zb,
+                                              int u, uint32_t p, uint32_t x, uint32_t xinv, const uint32_t* s_off,
+                                              uint32_t& g_out) {
+  const int2 st = cst[u >> 3];
+  uint32_t g = (uint32_t)st.x;
+  int64_t jj = (int64_t)(uint32_t)st.y - 8 + (u & 7);
+  uint32_t m = J.segs[g].m;
+  while (jj > (int64_t)m) {
+    jj -= (int64_t)m + 1;
+    m = J.segs[++g].m;
+  }
+  uint32_t q, r;
+  divmod_x((uint32_t)jj, x, xinv, q, r);
+  MinRec rec;
+  rec.key = (uint64_t)K[u] - 1;
+  rec.pos = J.segs[g].shift + p * q + s_off[r];
+  rec.segz = (g << 1) | zb[u];
+  g_out = g;
+  return rec;
+}
+
+// One atomic per distinct segment among the warp's lanes (g = ~0: no record).
+__device__ __forceinline__ void count_segments(uint32_t* seg_cnt, uint32_t g, int lane) {
+  const unsigned peers = __match_any_sync(0xffffffffu, g);
+  if (g != 0xFFFFFFFFu && __ffs(peers) - 1 == lane) atomicAdd(seg_cnt + g, (uint32_t)__popc(peers));
+}
+
 // A CTA takes tiles of WARPS * WT positions. All its threads gather, pack and
 // hash the tile (one barrier); then each warp evaluates the windows of its own
 // WT-position sub-tile and writes its minimizers in order. STAGED: into the
@@ -198,40 +429,47 @@ __device__ __forceinline__ uint64_t take64_le(uint64_t w0, uint64_t w1, uint32_t
 // compaction pass order them; tiles are strided over CTAs). Otherwise:
 // directly to their final place, found by a decoupled look-back over
 // sub-tiles taken from a ticket.
-template <int WARPS, typename KT, bool WIDE, bool STAGED>
-__global__ void __launch_bounds__(WARPS * 32) sketch_kernel(SketchArgs a) {
+template <int WARPS, typename KT, bool WIDE, bool STAGED, int MW>
+__global__ void __launch_bounds__(WARPS * 32) sketch_kernel(const __grid_constant__ SketchArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int BLOCK = WARPS * 32;
   const int WT = a.T;                         // owned positions per warp
   const int T = WARPS * WT;                   // owned positions per CTA tile
   const SketchJob& J = a.job;
   const int k = J.k, w = J.w;
-  const TileLayout Lt = tile_layout(WARPS, WT, k, w, (int)sizeof(KT));
+  const TileLayout Lt = tile_layout(WARPS, WT, k, w, (int)sizeof(KT), MW);
   const int n_keys = Lt.n_keys, n_codes = Lt.n_codes, n_groups = Lt.n_groups, n_chunks = Lt.n_chunks;
   const int n_win_w = Lt.n_win_w;
   const int n_keys_w = WT + 2 * (w - 1);
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   KT* K = reinterpret_cast<KT*>(smem);
-  KT* SM = reinterpret_cast<KT*>(smem + Lt.off_sm) + (size_t)wid * 2 * n_keys_w;  // this warp's
-  KT* SX = SM + n_keys_w;
+  KT* SM = reinterpret_cast<KT*>(smem + Lt.off_sm) + (size_t)wid * Lt.warp_scr;  // this warp's
   uint64_t* F = reinterpret_cast<uint64_t*>(smem + Lt.off_f);
   uint64_t* Cw = reinterpret_cast<uint64_t*>(smem + Lt.off_c);
   int2* cst = reinterpret_cast<int2*>(smem + Lt.off_cst);
   uint32_t* Nm = reinterpret_cast<uint32_t*>(smem + Lt.off_nm);
   uint8_t* zb = smem + Lt.off_zb;
-  uint8_t* sel = smem + Lt.off_sel + wid * WT;
+  uint32_t* Vb = reinterpret_cast<uint32_t*>(smem + Lt.off_vb);
   uint16_t* list = reinterpret_cast<uint16_t*>(smem + Lt.off_list) + wid * WT;
   __shared__ uint32_t s_tile, s_gt;
-  __shared__ uint64_t bnd[kBndCache + 1];    // seg_voff[g_tile + i], i <= kBndCache
+  __shared__ uint32_t bnd[kBndCache + 1];    // seg_voff[g_tile + i] relative to the tile's first base
+  __shared__ uint8_t s_lut[256];             // byte -> 2-bit code, 4 for anything but ACGT/acgt
+  __shared__ uint32_t s_off[kMaxPattern];    // offsets of the pattern's 1s
+  __shared__ uint32_t s_delta[kMaxPattern];  // original-position step to the next kept base
 
   const uint64_t mask = (k >= 32) ? ~0ULL : ((1ULL << (2 * k)) - 1);
   const uint64_t nmask = (1ULL << k) - 1;
   const uint32_t top_shift = 64 - 2 * k;
   const int p = J.pat.p, x = J.pat.x;
+  const uint32_t xinv = 0xFFFFFFFFu / (uint32_t)x;
   const KT PALIN = palin_mark<KT>();
   const unsigned FULL = 0xffffffffu;
-  const unsigned lt = (1u << lane) - 1u;
   const uint64_t n_sub = a.n_tiles;           // status words are per warp sub-tile
+  for (int i = tid; i < 256; i += BLOCK) s_lut[i] = (uint8_t)base_code((uint8_t)i);
+  for (int i = tid; i < x; i += BLOCK) {
+    s_off[i] = (uint32_t)J.pat.off[i];
+    s_delta[i] = (uint32_t)(i + 1 < x ? J.pat.off[i + 1] - J.pat.off[i] : p + J.pat.off[0] - J.pat.off[i]);
+  }
 
   for (uint32_t iter = 0;; ++iter) {
     if (tid == 0) {
@@ -242,28 +480,33 @@ __global__ void __launch_bounds__(WARPS * 32) sketch_kernel(SketchArgs a) {
     __syncthreads();
     const uint64_t tile = s_tile;
     if (tile * WARPS >= n_sub) break;
-    for (int i = tid; i <= kBndCache; i += BLOCK)
-      bnd[i] = J.seg_voff[min((uint64_t)s_gt + i, (uint64_t)J.n_seg)];
-    __syncthreads();
     const int64_t A = (int64_t)(tile * (uint64_t)T);
     const int64_t v_first = A - (w - 1);
+    const uint64_t base_v = v_first < 0 ? 0 : (uint64_t)v_first;
+    for (int i = tid; i <= kBndCache; i += BLOCK) {
+      const uint64_t bv = J.seg_voff[min((uint64_t)s_gt + i, (uint64_t)J.n_seg)];
+      bnd[i] = bv <= base_v ? 0u : (uint32_t)min(bv - base_v, (uint64_t)0xFFFFFFFFu);
+    }
+    __syncthreads();
     const uint32_t g_tile = s_gt;
 
-    // ---- 1. gather 8 bases per thread step, pack 2-bit codes with shuffles
+    // ---- 1. gather 8 bases per thread step (2-bit codes from the byte table),
+    // pack each 32-base group from four lanes
     for (int c0 = 0; c0 < n_chunks; c0 += BLOCK) {
       if (c0 + wid * 32 >= n_chunks) break;   // warp-uniform: whole warp idle
       const int c = c0 + tid;
       const bool act = c < n_chunks;
       const int64_t v0 = v_first + 8 * (int64_t)c;
-      uint32_t f16 = 0, c16 = 0, n8 = 0xFFu;
+      uint32_t f16 = 0, n8 = 0xFFu;
       int2 state = make_int2(-1, 0);
       if (act && v0 + 8 > 0 && v0 < (int64_t)J.V && 8 * c < n_codes) {
         n8 = 0;
         const uint64_t vs = v0 < 0 ? 0 : (uint64_t)v0;
-        // segment of vs: bisect the cached boundaries of the tile's first
-        // kBndCache segments (global memory only past them)
+        const uint32_t vr = (uint32_t)(vs - base_v);
+        // segment of vs: the cached boundaries of the tile's first kBndCache
+        // segments (global memory only past them)
         uint32_t g;
-        if (bnd[kBndCache] <= vs && g_tile + kBndCache < J.n_seg) {
+        if (bnd[kBndCache] <= vr && g_tile + kBndCache < J.n_seg) {
           uint32_t lo = g_tile + kBndCache, hi = J.n_seg;
           while (hi - lo > 1) {
             const uint32_t mid = (lo + hi) >> 1;
@@ -271,65 +514,82 @@ __global__ void __launch_bounds__(WARPS * 32) sketch_kernel(SketchArgs a) {
           }
           g = lo;
         } else {
-          uint32_t lo = 0, hi = kBndCache;
-          while (hi - lo > 1) {
-            const uint32_t mid = (lo + hi) >> 1;
-            if (bnd[mid] <= vs) lo = mid; else hi = mid;
-          }
+          uint32_t lo = 0;
+#pragma unroll
+          for (int step = kBndCache / 2; step > 0; step >>= 1)
+            if (bnd[lo + step] <= vr) lo += step;
           g = g_tile + lo;
         }
-        SegDesc d = J.segs[g];
-        uint64_t gend = J.seg_voff[g + 1];
+        const SegDesc d0 = J.segs[g];
         uint32_t j = (uint32_t)(vs - J.seg_voff[g]);
         // (segment, index of the chunk's first base in it + 8): biased because
         // the stream's first chunk starts before position 0
         state = make_int2((int)g, (int)(j + 8u - (uint32_t)((int64_t)vs - v0)));
-        uint32_t q = j / (uint32_t)x, r = j - q * (uint32_t)x;
-        const uint8_t* src = J.bytes + d.byte_off;
+        uint32_t q, r;
+        divmod_x(j, (uint32_t)x, xinv, q, r);
+        if (v0 >= 0 && j + 8 <= d0.m && 8 * c + 8 <= n_codes) {
+          // all eight are bases of segment g
+          const uint8_t* src = J.bytes + d0.byte_off + d0.shift;
+          uint32_t o = (uint32_t)p * q + s_off[r];
+          if (x == 1) {
 #pragma unroll
-        for (int dd = 0; dd < 8; ++dd) {
-          const int64_t v = v0 + dd;
-          uint32_t code = 4;
-          if (v >= 0 && (uint64_t)v < J.V && 8 * c + dd < n_codes) {
-            if ((uint64_t)v >= gend) {
-              ++g;
-              d = J.segs[g];
-              src = J.bytes + d.byte_off;
-              gend = J.seg_voff[g + 1];
-              j = 0; q = 0; r = 0;
+            for (int dd = 0; dd < 8; ++dd) {
+              const uint32_t e = s_lut[__ldg(src + o + (uint32_t)p * dd)];
+              f16 |= (e & 3u) << (14 - 2 * dd);
+              n8 |= (e >> 2) << dd;
             }
-            if (j < d.m) {
-              code = base_code(__ldg(src + d.shift + (uint64_t)p * q + (uint32_t)J.pat.off[r]));
-              if (code == 4 && (d.flags & kSegCapped) && J.read_flag) J.read_flag[d.read] = 1u;
-            }
-            ++j;
-            if (++r == (uint32_t)x) { r = 0; ++q; }
-          }
-          if (code < 4) {
-            f16 |= code << (14 - 2 * dd);
-            c16 |= (3u - code) << (2 * dd);
           } else {
-            n8 |= 1u << dd;
+#pragma unroll
+            for (int dd = 0; dd < 8; ++dd) {
+              const uint32_t e = s_lut[__ldg(src + o)];
+              f16 |= (e & 3u) << (14 - 2 * dd);
+              n8 |= (e >> 2) << dd;
+              o += s_delta[r];
+              r = r + 1 == (uint32_t)x ? 0 : r + 1;
+            }
+          }
+          if (n8 && (d0.flags & kSegCapped) && J.read_flag) J.read_flag[d0.read] = 1u;
+        } else {
+          SegDesc d = d0;
+          uint64_t gend = J.seg_voff[g + 1];
+          const uint8_t* src = J.bytes + d.byte_off + d.shift;
+#pragma unroll
+          for (int dd = 0; dd < 8; ++dd) {
+            const int64_t v = v0 + dd;
+            uint32_t e = 4;
+            if (v >= 0 && (uint64_t)v < J.V && 8 * c + dd < n_codes) {
+              if ((uint64_t)v >= gend) {
+                ++g;
+                d = J.segs[g];
+                src = J.bytes + d.byte_off + d.shift;
+                gend = J.seg_voff[g + 1];
+                j = 0; q = 0; r = 0;
+              }
+              if (j < d.m) {
+                e = s_lut[__ldg(src + (uint64_t)p * q + s_off[r])];
+                if (e == 4 && (d.flags & kSegCapped) && J.read_flag) J.read_flag[d.read] = 1u;
+              }
+              ++j;
+              if (++r == (uint32_t)x) { r = 0; ++q; }
+            }
+            f16 |= (e & 3u) << (14 - 2 * dd);
+            n8 |= (e >> 2) << dd;
           }
         }
       }
       if (act) cst[c] = state;
       // four consecutive lanes hold the four chunks of one 32-base group
       // (n_chunks is a multiple of 4: a group is all active or all idle)
-      const int part = lane & 3;
-      uint64_t fw = (uint64_t)f16 << (48 - 16 * part);
-      uint64_t cw = (uint64_t)c16 << (16 * part);
-      uint32_t nw = n8 << (8 * part);
-      fw |= __shfl_xor_sync(FULL, fw, 1);
-      cw |= __shfl_xor_sync(FULL, cw, 1);
-      nw |= __shfl_xor_sync(FULL, nw, 1);
-      fw |= __shfl_xor_sync(FULL, fw, 2);
-      cw |= __shfl_xor_sync(FULL, cw, 2);
-      nw |= __shfl_xor_sync(FULL, nw, 2);
-      if (act && part == 0) {
+      const uint32_t v = f16 | (n8 << 16);
+      const int gl = lane & ~3;
+      const uint32_t v1 = __shfl_sync(FULL, v, gl + 1);
+      const uint32_t v2 = __shfl_sync(FULL, v, gl + 2);
+      const uint32_t v3 = __shfl_sync(FULL, v, gl + 3);
+      if (act && (lane & 3) == 0) {
+        const uint64_t fw = ((uint64_t)((v << 16) | (v1 & 0xFFFFu)) << 32) | ((v2 << 16) | (v3 & 0xFFFFu));
         F[c >> 2] = fw;
-        Cw[c >> 2] = cw;
-        Nm[c >> 2] = nw;
+        Cw[c >> 2] = ~rev_pairs64(fw);   // complements, little-endian (fields under N unused)
+        Nm[c >> 2] = (v >> 16) | ((v1 >> 16) << 8) | ((v2 >> 16) << 16) | ((v3 >> 16) << 24);
       }
     }
     if (tid == 0) {  // one spare group so that every k-mer reads two words
@@ -337,123 +597,105 @@ __global__ void __launch_bounds__(WARPS * 32) sketch_kernel(SketchArgs a) {
       Cw[n_groups] = 0;
       Nm[n_groups] = 0xFFFFFFFFu;
     }
+    if (tid < 3) Vb[n_keys / 32 + tid] = 0;   // words past the last key (rewritten below where keys exist)
     __syncthreads();
 
-    // ---- 2. canonical k-mer keys, one position per thread (funnel shifts)
-    for (int i0 = 0; i0 < n_keys; i0 += BLOCK) {
-      if (i0 + wid * 32 >= n_keys) break;
-      const int i = i0 + tid;
-      if (i < n_keys) {
+    // ---- 2. canonical k-mer keys, four consecutive positions per thread: one
+    // 64-bit window of each strand's packed codes (32 bases) holds all four
+    const int n_quads = (n_keys + 3) >> 2;
+    for (int q0 = 0; q0 < n_quads; q0 += BLOCK) {
+      if (q0 + wid * 32 >= n_quads) break;    // warp-uniform
+      const int qd = q0 + tid;
+      const int i = 4 * qd;
+      uint32_t valid4 = 0;
+      if (qd < n_quads) {
         const int g = i >> 5, b = i & 31;
-        const uint64_t nn = (((uint64_t)Nm[g + 1] << 32) | Nm[g]) >> b;
-        KT kk = 0;
-        uint8_t z = 0;
-        if ((nn & nmask) == 0) {
-          const uint64_t fwd = take64_be(F[g], F[g + 1], 2 * b) >> top_shift;
-          const uint64_t rev = take64_le(Cw[g], Cw[g + 1], 2 * b) & mask;
-          if (fwd == rev) {
-            kk = PALIN;
-          } else {
-            z = rev < fwd;
-            kk = (KT)(wang_mix<WIDE>(z ? rev : fwd, mask) + 1);
+        const uint32_t nn = __funnelshift_r(Nm[g], Nm[g + 1], b);
+        const uint64_t tb = take64_be(F[g], F[g + 1], 2 * b);   // base i + m at bits 63 - 2m, 62 - 2m
+        const uint64_t tl = take64_le(Cw[g], Cw[g + 1], 2 * b);  // its complement at bits 2m, 2m + 1
+        KT kq[4];
+        uint32_t zq = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          KT kk = 0;
+          if (((nn >> j) & (uint32_t)nmask) == 0) {
+            uint64_t fwd, rev;
+            if (WIDE) {     // 2k > 32: every shift below is under 32
+              const uint32_t sh = top_shift - 2 * j;
+              const uint32_t th = (uint32_t)(tb >> 32);
+              fwd = ((uint64_t)((th >> sh) & (uint32_t)(mask >> 32)) << 32) | __funnelshift_r((uint32_t)tb, th, sh);
+              const uint64_t rs = tl >> (2 * j);
+              rev = ((uint64_t)((uint32_t)(rs >> 32) & (uint32_t)(mask >> 32)) << 32) | (uint32_t)rs;
+            } else {
+              fwd = (uint32_t)(tb >> (top_shift - 2 * j)) & (uint32_t)mask;
+              rev = (uint32_t)(tl >> (2 * j)) & (uint32_t)mask;
+            }
+            if (fwd == rev) {
+              kk = PALIN;
+            } else {
+              const bool z = rev < fwd;
+              zq |= (uint32_t)z << (8 * j);
+              kk = (KT)(wang_mix<WIDE>(z ? rev : fwd, mask) + 1);
+              valid4 |= 1u << j;
+            }
           }
+          kq[j] = kk;
         }
-        K[i] = kk;
-        zb[i] = z;
+        if (i + 3 < n_keys) {
+          if (sizeof(KT) == 8) {
+            reinterpret_cast<ulonglong2*>(K + i)[0] = make_ulonglong2(kq[0], kq[1]);
+            reinterpret_cast<ulonglong2*>(K + i)[1] = make_ulonglong2(kq[2], kq[3]);
+          } else {
+            *reinterpret_cast<uint4*>(K + i) = make_uint4((uint32_t)kq[0], (uint32_t)kq[1], (uint32_t)kq[2],
+                                                          (uint32_t)kq[3]);
+          }
+          *reinterpret_cast<uint32_t*>(zb + i) = zq;
+        } else {
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (i + j < n_keys) {
+              K[i + j] = kq[j];
+              zb[i + j] = (uint8_t)(zq >> (8 * j));
+            }
+          valid4 &= (1u << (n_keys - i)) - 1u;
+        }
       }
+      // usable-key bits of 32 positions from eight lanes
+      uint32_t vb = valid4 << (4 * (lane & 7));
+      vb |= __shfl_xor_sync(FULL, vb, 1);
+      vb |= __shfl_xor_sync(FULL, vb, 2);
+      vb |= __shfl_xor_sync(FULL, vb, 4);
+      if ((lane & 7) == 0 && qd < n_quads) Vb[qd >> 3] = vb;
     }
     __syncthreads();
 
-    // ---- 3. this warp's window minima over keys [wo, wo + n_keys_w) of the
-    // tile, wo = 256 * warp (van Herk / Gil-Werman: lane = one block of w
-    // keys; suffix minima backwards, prefix minima forwards with the next
-    // block's running prefix taken from the next lane).
+    // ---- 3/4. window minima and the minimizer test over this warp's keys
+    // [wo, wo + n_keys_w) of the tile
     const int wo = wid * WT;
     const KT* Kw = K + wo;
-    {
-      const int nb = (n_keys_w + w - 1) / w;
-      for (int gb = 0; gb < nb; gb += 31) {
-        const int b = gb + lane;
-        const int s = b * w;
-        const bool live = b < nb;
-        KT m = PALIN;
-        for (int t = w - 1; t >= 0; --t) {
-          const int i = s + t;
-          if (live && i < n_keys_w) { m = min(m, Kw[i]); SM[i] = m; }
-        }
-        __syncwarp();
-        KT pm = PALIN;
-        for (int t = 0; t < w; ++t) {
-          const int i = s + t;
-          const KT kv = (live && i < n_keys_w) ? Kw[i] : PALIN;
-          const KT nxt = __shfl_down_sync(FULL, pm, 1);   // next block's prefix over offsets < t
-          if (lane < 31 && live && i < n_win_w && t) SM[i] = min(SM[i], nxt);
-          pm = min(pm, kv);
-        }
-        __syncwarp();
-      }
+    uint32_t cnt;
+    if constexpr (MW > 0) {
+      cnt = window_select_reg<MW, KT>(Kw, SM, Vb, wo, w, WT, lane, list);
+    } else {
+      cnt = window_select_smem<KT>(Kw, SM, SM + n_keys_w, smem + Lt.off_sel + wid * WT, w, n_keys_w, n_win_w, WT,
+                                   lane, list);
     }
 
-    // ---- 4. largest window minimum covering each owned position; the test
-    {
-      const int nb = (n_win_w + w - 1) / w;
-      for (int gb = 0; gb < nb; gb += 31) {
-        const int b = gb + lane;
-        const int s = b * w;
-        const bool live = b < nb;
-        KT m = 0;
-        for (int t = w - 1; t >= 0; --t) {
-          const int i = s + t;
-          if (live && i < n_win_w) { m = max(m, SM[i]); SX[i] = m; }
-        }
-        __syncwarp();
-        KT px = 0;
-        for (int t = 0; t < w; ++t) {
-          const int i = s + t;
-          const KT mv = (live && i < n_win_w) ? SM[i] : (KT)0;
-          const KT nxt = __shfl_down_sync(FULL, px, 1);
-          if (lane < 31 && live && i < WT) {
-            const KT mx = t == 0 ? SX[i] : max(SX[i], nxt);
-            const KT kk = Kw[i + w - 1];
-            sel[i] = (kk != 0 && kk != PALIN && kk == mx) ? 1 : 0;
-          }
-          px = max(px, mv);
-        }
-        __syncwarp();
-      }
-    }
-
-    // ---- 5. compact the selected positions, then ordered output through a
-    // warp-parallel decoupled look-back over sub-tiles
-    uint32_t cnt = 0;
-    for (int o0 = 0; o0 < WT; o0 += 32) {
-      const bool f = o0 + lane < WT && sel[o0 + lane] != 0;
-      const unsigned bal = __ballot_sync(FULL, f);
-      if (f) list[cnt + __popc(bal & lt)] = (uint16_t)(o0 + lane);
-      cnt += __popc(bal);
-    }
-    __syncwarp();
+    // ---- 5. records of the selected positions, in order: staged per sub-tile,
+    // or at their final place after a warp-parallel decoupled look-back
     const uint64_t sub = tile * WARPS + wid;
     uint64_t excl = 0;
     if (STAGED && sub < n_sub) {
       if (lane == 0) a.sub_cnt[sub] = cnt;
-      for (uint32_t li = lane; li < cnt; li += 32) {
-        const int u = wo + list[li] + w - 1;       // base / k-mer index inside the tile
-        const int2 st = cst[u >> 3];
-        uint32_t g = (uint32_t)st.x;
-        int64_t jj = (int64_t)(uint32_t)st.y - 8 + (u & 7);
-        SegDesc d = J.segs[g];
-        while (jj > (int64_t)d.m) {
-          jj -= (int64_t)d.m + 1;
-          d = J.segs[++g];
+      for (uint32_t l0 = 0; l0 < cnt; l0 += 32) {
+        const uint32_t li = l0 + lane;
+        uint32_t g = 0xFFFFFFFFu;
+        if (li < cnt) {
+          const MinRec rec = make_record<KT>(J, cst, K, zb, wo + list[li] + w - 1, (uint32_t)p, (uint32_t)x, xinv,
+                                             s_off, g);
+          a.staging[sub * (uint64_t)WT + li] = rec;
         }
-        const uint32_t qq = (uint32_t)jj / (uint32_t)x;
-        MinRec rec;
-        rec.key = (uint64_t)K[u] - 1;
-        rec.pos = d.shift + (uint32_t)p * qq + (uint32_t)J.pat.off[(uint32_t)jj - qq * (uint32_t)x];
-        rec.segz = (g << 1) | zb[u];
-        a.staging[sub * (uint64_t)WT + li] = rec;
-        if (J.seg_cnt) atomicAdd(J.seg_cnt + g, 1u);
+        if (J.seg_cnt) count_segments(J.seg_cnt, g, lane);
       }
     } else if (!STAGED && sub < n_sub) {
       if (sub == 0) {
@@ -486,37 +728,26 @@ __global__ void __launch_bounds__(WARPS * 32) sketch_kernel(SketchArgs a) {
         if (lane == 0) st_release_u64(a.tile_status + sub, kFlagIncl | (excl + cnt));
       }
       if (lane == 0 && sub == n_sub - 1) *a.total = excl + cnt;
-      for (uint32_t li = lane; li < cnt; li += 32) {
-        const int u = wo + list[li] + w - 1;       // base / k-mer index inside the tile
-        const int2 st = cst[u >> 3];
-        uint32_t g = (uint32_t)st.x;
-        int64_t jj = (int64_t)(uint32_t)st.y - 8 + (u & 7);
-        SegDesc d = J.segs[g];
-        while (jj > (int64_t)d.m) {
-          jj -= (int64_t)d.m + 1;
-          d = J.segs[++g];
+      for (uint32_t l0 = 0; l0 < cnt; l0 += 32) {
+        const uint32_t li = l0 + lane;
+        uint32_t g = 0xFFFFFFFFu;
+        if (li < cnt) {
+          const MinRec rec = make_record<KT>(J, cst, K, zb, wo + list[li] + w - 1, (uint32_t)p, (uint32_t)x, xinv,
+                                             s_off, g);
+          const uint64_t at = excl + li;
+          if (at < J.out_cap) J.out[at] = rec;
         }
-        const uint32_t qq = (uint32_t)jj / (uint32_t)x;
-        const uint32_t orig = d.shift + (uint32_t)p * qq + (uint32_t)J.pat.off[(uint32_t)jj - qq * (uint32_t)x];
-        const uint64_t at = excl + li;
-        if (at < J.out_cap) {
-          MinRec rec;
-          rec.key = (uint64_t)K[u] - 1;
-          rec.pos = orig;
-          rec.segz = (g << 1) | zb[u];
-          J.out[at] = rec;
-        }
-        if (J.seg_cnt) atomicAdd(J.seg_cnt + g, 1u);
+        if (J.seg_cnt) count_segments(J.seg_cnt, g, lane);
       }
     }
     __syncthreads();  // the tile's shared memory is rewritten by the next tile
   }
 }
 
-template <int WARPS, typename KT, bool WIDE, bool STAGED>
-int launch_sketch_kt(const SketchArgs& a, cudaStream_t st) {
-  auto sketch = sketch_kernel<WARPS, KT, WIDE, STAGED>;
-  const size_t smem = tile_layout(WARPS, a.T, a.job.k, a.job.w, (int)sizeof(KT)).bytes;
+template <int WARPS, typename KT, bool WIDE, bool STAGED, int MW>
+int launch_sketch_mw(const SketchArgs& a, cudaStream_t st) {
+  auto sketch = sketch_kernel<WARPS, KT, WIDE, STAGED, MW>;
+  const size_t smem = tile_layout(WARPS, a.T, a.job.k, a.job.w, (int)sizeof(KT), MW).bytes;
   GOD_CK(cudaFuncSetAttribute(sketch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   GOD_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sketch, WARPS * 32, smem));
@@ -529,6 +760,15 @@ int launch_sketch_kt(const SketchArgs& a, cudaStream_t st) {
   const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(want, ctas_needed));
   GOD_LAUNCH(sketch, grid, WARPS * 32, smem, st, a);
   return GOD_OK;
+}
+
+template <int WARPS, typename KT, bool WIDE, bool STAGED>
+int launch_sketch_kt(const SketchArgs& a, cudaStream_t st) {
+  switch (window_mw(a.job.w)) {
+    case 12: return launch_sketch_mw<WARPS, KT, WIDE, STAGED, 12>(a, st);
+    case 20: return launch_sketch_mw<WARPS, KT, WIDE, STAGED, 20>(a, st);
+    default: return launch_sketch_mw<WARPS, KT, WIDE, STAGED, 0>(a, st);
+  }
 }
 
 template <int WARPS, bool STAGED>
@@ -556,10 +796,12 @@ int launch_sketch(SketchArgs a, const SketchTune& tn, cudaStream_t st) {
   const uint64_t n_ctiles = (a.n_tiles + warps - 1) / warps;
   GOD_LAUNCH(tile_first_segment, (unsigned)std::min<uint64_t>((n_ctiles + 255) / 256, 65535), 256, 0, st,
              a.job.seg_voff, a.job.n_seg, a.job.V, (uint64_t)a.T * warps, a.job.w, n_ctiles, a.tile_seg);
-  switch (tn.threads) {
-    case 128: return launch_sketch_w<4, STAGED>(a, st);
-    default: return launch_sketch_w<8, STAGED>(a, st);
+  if (tn.threads == 128) {
+    if constexpr (STAGED) return launch_sketch_w<4, STAGED>(a, st);
+    set_error("sketch: the look-back mode runs 256-thread CTAs");
+    return GOD_EINVAL;
   }
+  return launch_sketch_w<8, STAGED>(a, st);
 }
 
 // Staged records of each sub-tile -> their ordered place (warp per sub-tile).
@@ -582,7 +824,8 @@ SketchTune clamp_tune(SketchTune tn, int k, int w) {
   // shrink until the tile workspace fits one CTA's shared memory
   while (true) {
     tn.tile = sub_tile_for(tn.threads / 32, k, w, tn.chunks);
-    if (tile_layout(tn.threads / 32, tn.tile, k, w, kt).bytes + 4096 <= 227 * 1024 || tn.chunks == 1) break;
+    if (tile_layout(tn.threads / 32, tn.tile, k, w, kt, window_mw(w)).bytes + 4096 <= 227 * 1024 || tn.chunks == 1)
+      break;
     tn.chunks = 1;
   }
   return tn;
