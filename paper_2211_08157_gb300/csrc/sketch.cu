@@ -165,9 +165,16 @@ __host__ __device__ inline int sub_tile_for(int warps, int k, int w, int chunks 
   return wt < 64 ? 64 : wt;
 }
 
-// Window stage of the kernel: blocks of up to MW keys in registers (MW = 12
-// or 20), or shared-memory passes for any w (MW = 0).
-__host__ __device__ inline int window_mw(int w) { return w <= 12 ? 12 : w <= 20 ? 20 : 0; }
+// Window stage of the kernel, by variant WV: blocks of exactly WV keys in
+// registers (WV > 0: the window lengths of the standard presets, w = 11 and 19
+// for k > 16 and w = 10 for k <= 15), blocks of up to -WV keys (WV = -12 or
+// -20), or shared-memory passes for any w (WV = 0).
+__host__ __device__ inline int window_variant(int k, int w) {
+  if (k > 16 && (w == 11 || w == 19)) return w;
+  if (k <= 15 && w == 10) return w;
+  return w <= 12 ? -12 : w <= 20 ? -20 : 0;
+}
+__host__ __device__ constexpr int window_regs(int wv) { return wv < 0 ? -wv : wv; }
 
 // Shared-memory layout of one CTA tile of T = WARPS * WT owned positions
 // (host and device agree on it).
@@ -429,7 +436,7 @@ __device__ __forceinline__ void count_segments(uint32_t* seg_cnt, uint32_t g, in
 // compaction pass order them; tiles are strided over CTAs). Otherwise:
 // directly to their final place, found by a decoupled look-back over
 // sub-tiles taken from a ticket.
-template <int WARPS, typename KT, bool WIDE, bool STAGED, int MW>
+template <int WARPS, typename KT, bool WIDE, bool STAGED, int WV>
 __global__ void __launch_bounds__(WARPS * 32) sketch_kernel(const __grid_constant__ SketchArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int BLOCK = WARPS * 32;
@@ -437,6 +444,7 @@ __global__ void __launch_bounds__(WARPS * 32) sketch_kernel(const __grid_constan
   const int T = WARPS * WT;                   // owned positions per CTA tile
   const SketchJob& J = a.job;
   const int k = J.k, w = J.w;
+  constexpr int MW = window_regs(WV);
   const TileLayout Lt = tile_layout(WARPS, WT, k, w, (int)sizeof(KT), MW);
   const int n_keys = Lt.n_keys, n_codes = Lt.n_codes, n_groups = Lt.n_groups, n_chunks = Lt.n_chunks;
   const int n_win_w = Lt.n_win_w;
@@ -675,7 +683,7 @@ __global__ void __launch_bounds__(WARPS * 32) sketch_kernel(const __grid_constan
     const KT* Kw = K + wo;
     uint32_t cnt;
     if constexpr (MW > 0) {
-      cnt = window_select_reg<MW, KT>(Kw, SM, Vb, wo, w, WT, lane, list);
+      cnt = window_select_reg<MW, KT>(Kw, SM, Vb, wo, WV > 0 ? WV : w, WT, lane, list);
     } else {
       cnt = window_select_smem<KT>(Kw, SM, SM + n_keys_w, smem + Lt.off_sel + wid * WT, w, n_keys_w, n_win_w, WT,
                                    lane, list);
@@ -744,10 +752,10 @@ __global__ void __launch_bounds__(WARPS * 32) sketch_kernel(const __grid_constan
   }
 }
 
-template <int WARPS, typename KT, bool WIDE, bool STAGED, int MW>
+template <int WARPS, typename KT, bool WIDE, bool STAGED, int WV>
 int launch_sketch_mw(const SketchArgs& a, cudaStream_t st) {
-  auto sketch = sketch_kernel<WARPS, KT, WIDE, STAGED, MW>;
-  const size_t smem = tile_layout(WARPS, a.T, a.job.k, a.job.w, (int)sizeof(KT), MW).bytes;
+  auto sketch = sketch_kernel<WARPS, KT, WIDE, STAGED, WV>;
+  const size_t smem = tile_layout(WARPS, a.T, a.job.k, a.job.w, (int)sizeof(KT), window_regs(WV)).bytes;
   GOD_CK(cudaFuncSetAttribute(sketch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   GOD_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sketch, WARPS * 32, smem));
@@ -764,11 +772,17 @@ int launch_sketch_mw(const SketchArgs& a, cudaStream_t st) {
 
 template <int WARPS, typename KT, bool WIDE, bool STAGED>
 int launch_sketch_kt(const SketchArgs& a, cudaStream_t st) {
-  switch (window_mw(a.job.w)) {
-    case 12: return launch_sketch_mw<WARPS, KT, WIDE, STAGED, 12>(a, st);
-    case 20: return launch_sketch_mw<WARPS, KT, WIDE, STAGED, 20>(a, st);
-    default: return launch_sketch_mw<WARPS, KT, WIDE, STAGED, 0>(a, st);
+  const int wv = window_variant(a.job.k, a.job.w);
+  if constexpr (WIDE) {
+    if (wv == 11) return launch_sketch_mw<WARPS, KT, WIDE, STAGED, 11>(a, st);
+    if (wv == 19) return launch_sketch_mw<WARPS, KT, WIDE, STAGED, 19>(a, st);
   }
+  if constexpr (sizeof(KT) == 4) {
+    if (wv == 10) return launch_sketch_mw<WARPS, KT, WIDE, STAGED, 10>(a, st);
+  }
+  if (wv == -12) return launch_sketch_mw<WARPS, KT, WIDE, STAGED, -12>(a, st);
+  if (wv == -20) return launch_sketch_mw<WARPS, KT, WIDE, STAGED, -20>(a, st);
+  return launch_sketch_mw<WARPS, KT, WIDE, STAGED, 0>(a, st);
 }
 
 template <int WARPS, bool STAGED>
@@ -824,7 +838,8 @@ SketchTune clamp_tune(SketchTune tn, int k, int w) {
   // shrink until the tile workspace fits one CTA's shared memory
   while (true) {
     tn.tile = sub_tile_for(tn.threads / 32, k, w, tn.chunks);
-    if (tile_layout(tn.threads / 32, tn.tile, k, w, kt, window_mw(w)).bytes + 4096 <= 227 * 1024 || tn.chunks == 1)
+    if (tile_layout(tn.threads / 32, tn.tile, k, w, kt, window_regs(window_variant(k, w))).bytes + 4096 <= 227 * 1024 ||
+        tn.chunks == 1)
       break;
     tn.chunks = 1;
   }
