@@ -214,8 +214,10 @@ struct DeviceIndex {           // what lookup kernels need, by value
   const uint64_t* keys;        // n_keys ascending
   const uint32_t* start;       // n_keys + 1
   const uint64_t* ent;         // (pos << 1) | z
-  const ulonglong2* ht;        // {key, start | count << 32}
-  uint64_t ht_mask;
+  // hash table: 2^ht_lc slots of one word [key >> ht_lc | displacement from
+  // the home slot (ht_db bits) | rank in keys (ht_rb bits)], ~0 when empty
+  const uint64_t* ht;
+  uint32_t ht_lc, ht_db, ht_rb;
   uint64_t n_keys;
   const RmiLeaf* leaves;       // null without a learned index
   const RmiRoot* root;         // device copy
@@ -236,8 +238,9 @@ struct god_index {
   uint64_t* d_keys;
   uint32_t* d_start;
   uint64_t* d_ent;
-  ulonglong2* d_ht;
+  uint64_t* d_ht;
   uint64_t ht_cap;
+  uint32_t ht_lc, ht_db, ht_rb;
   god_params params;
   // learned index
   int has_rmi;

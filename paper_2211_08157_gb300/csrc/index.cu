@@ -6,7 +6,8 @@
 //   keys[U]     kept keys ascending,
 //   start[U+1]  offsets of each key's entries,
 //   ent[E]      (ref_pos << 1) | z, ascending within a key,
-// plus an open-addressing hash table key -> (start, count) at load <= 1/2.
+// plus an open-addressing hash table key -> rank at load <= 1/2 (one 64-bit
+// word per slot; the rank gives (start, count)).
 // The learned index (built in rmi.cu) predicts a key's rank in keys[] instead.
 #include <algorithm>
 
@@ -31,64 +32,72 @@ __global__ void split_records(const MinRec* rec, uint64_t n, uint64_t* keys, uin
   }
 }
 
-__global__ void mark_heads(const uint64_t* keys, uint64_t n, uint32_t* head) {
-  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
-    head[i] = (i == 0 || keys[i] != keys[i - 1]) ? 1u : 0u;
-}
-
-// run_excl[i] = heads before i (n + 1 entries). Heads record their run start.
-__global__ void run_starts(const uint32_t* head, const uint64_t* run_excl, uint64_t n, uint64_t* run_start,
-                           uint64_t n_runs) {
+// Runs of equal keys in the sorted array: the first element of each run
+// (its head) finds the run's end by galloping then bisecting, and records
+// rv[i] = 1 << 32 | length for a kept run (length <= max_occ), 0 otherwise.
+// An exclusive scan of rv then gives every kept run its key rank (high half)
+// and its first entry (low half): lengths sum to at most n < 2^32, so the low
+// half never carries into the high one.
+__global__ void run_heads(const uint64_t* __restrict__ keys, uint64_t n, uint32_t max_occ, uint64_t* __restrict__ rv) {
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-    if (head[i]) run_start[run_excl[i]] = i;
+    const uint64_t key = keys[i];
+    uint64_t v = 0;
+    if (i == 0 || keys[i - 1] != key) {
+      uint64_t step = 1;
+      while (i + step < n && keys[i + step] == key) step <<= 1;
+      uint64_t lo = i + (step >> 1), hi = std::min<uint64_t>(i + step, n);   // keys[lo] == key, end in (lo, hi]
+      while (hi - lo > 1) {
+        const uint64_t mid = (lo + hi) >> 1;
+        if (keys[mid] == key) lo = mid; else hi = mid;
+      }
+      const uint64_t len = hi - i;
+      if (len <= max_occ) v = (1ULL << 32) | len;
+    }
+    rv[i] = v;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) run_start[n_runs] = n;
 }
 
-__global__ void run_keep(const uint64_t* run_start, uint64_t n_runs, uint32_t max_occ, uint32_t* kept,
-                         uint64_t* kept_len) {
-  for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < n_runs; r += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t len = run_start[r + 1] - run_start[r];
-    const bool k = len <= max_occ;
-    kept[r] = k;
-    kept_len[r] = k ? len : 0;
-  }
-}
-
-__global__ void emit_keys(const uint64_t* keys, const uint64_t* run_start, const uint32_t* kept,
-                          const uint64_t* kept_rank, const uint64_t* ent_off, uint64_t n_runs, uint64_t* out_keys,
-                          uint32_t* out_start) {
-  for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < n_runs; r += (uint64_t)gridDim.x * blockDim.x) {
-    if (kept[r]) {
-      out_keys[kept_rank[r]] = keys[run_start[r]];
-      out_start[kept_rank[r]] = (uint32_t)ent_off[r];
+// Kept runs -> keys[U], start[U + 1], ent[E].
+__global__ void emit_runs(const uint64_t* __restrict__ keys, const uint64_t* __restrict__ vals, uint64_t n,
+                          const uint64_t* __restrict__ rv, const uint64_t* __restrict__ roff,
+                          uint64_t* __restrict__ out_keys, uint32_t* __restrict__ out_start,
+                          uint64_t* __restrict__ out_ent) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t v = rv[i];
+    if (v) {
+      const uint64_t o = roff[i];
+      const uint32_t u = (uint32_t)(o >> 32), e = (uint32_t)o, len = (uint32_t)v;
+      out_keys[u] = keys[i];
+      out_start[u] = e;
+      for (uint32_t j = 0; j < len; ++j) out_ent[(uint64_t)e + j] = vals[i + j];
     }
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) out_start[kept_rank[n_runs]] = (uint32_t)ent_off[n_runs];
-}
-
-__global__ void emit_entries(const uint64_t* vals, const uint64_t* run_excl, const uint64_t* run_start,
-                             const uint32_t* kept, const uint64_t* ent_off, uint64_t n, uint64_t* out_ent) {
-  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t r = run_excl[i + 1] - 1;  // heads in [0, i] minus one
-    if (kept[r]) out_ent[ent_off[r] + (i - run_start[r])] = vals[i];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const uint64_t t = roff[n];
+    out_start[t >> 32] = (uint32_t)t;
   }
 }
 
-__global__ void ht_insert(const uint64_t* keys, const uint32_t* start, uint64_t n, ulonglong2* ht, uint64_t mask) {
-  for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < n; r += (uint64_t)gridDim.x * blockDim.x) {
+// Hash table insert of key rank r (linear probing, one CAS per probe). A
+// displacement past the field's range sets *overflow (the caller rebuilds a
+// larger table).
+__global__ void ht_insert(const uint64_t* __restrict__ keys, uint64_t U, uint64_t* ht, uint32_t lc, uint32_t db,
+                          uint32_t rb, int* overflow) {
+  const uint64_t mask = (1ULL << lc) - 1;
+  const uint64_t maxd = (1ULL << db) - 2;
+  for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < U; r += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t key = keys[r];
-    const uint64_t payload = (uint64_t)start[r] | ((uint64_t)(start[r + 1] - start[r]) << 32);
-    uint64_t slot = key & mask;
-    for (uint64_t probe = 0; probe <= mask; ++probe) {
-      unsigned long long* kp = reinterpret_cast<unsigned long long*>(&ht[slot].x);
-      const unsigned long long prev = atomicCAS(kp, (unsigned long long)kEmptyKey, (unsigned long long)key);
-      if (prev == kEmptyKey) {
-        ht[slot].y = payload;
+    const uint64_t h = key & mask, q = key >> lc;
+    bool placed = false;
+    for (uint64_t d = 0; d <= maxd; ++d) {
+      const unsigned long long word = (unsigned long long)((((q << db) | d) << rb) | r);
+      unsigned long long* slot = reinterpret_cast<unsigned long long*>(ht + ((h + d) & mask));
+      if (atomicCAS(slot, (unsigned long long)kEmptyKey, word) == kEmptyKey) {
+        placed = true;
         break;
       }
-      slot = (slot + 1) & mask;
     }
+    if (!placed) atomicExch(overflow, 1);
   }
 }
 
@@ -105,7 +114,7 @@ __global__ void __launch_bounds__(kThreads) lookup_kernel(DeviceIndex di, const 
   }
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t key = __ldg(keys + i * stride_words);
-    out[i] = VIA == 1 ? rmi_find(di, R, key) : ht_find(di.ht, di.ht_mask, key);
+    out[i] = VIA == 1 ? rmi_find(di, R, key) : ht_find(di, key);
   }
 }
 
@@ -115,7 +124,9 @@ DeviceIndex device_view(const god_index* idx, int via) {
   d.start = idx->d_start;
   d.ent = idx->d_ent;
   d.ht = idx->d_ht;
-  d.ht_mask = idx->ht_cap - 1;
+  d.ht_lc = idx->ht_lc;
+  d.ht_db = idx->ht_db;
+  d.ht_rb = idx->ht_rb;
   d.n_keys = idx->n_keys;
   d.leaves = (via == 1 && idx->has_rmi) ? idx->d_leaves : nullptr;
   d.root = (via == 1 && idx->has_rmi) ? idx->d_root : nullptr;
@@ -177,63 +188,72 @@ int build_index_device(god_index* idx, const uint8_t* d_ref, uint64_t len, cudaS
   rec.release();
   GOD_TRY(radix_sort_pairs(keys.p, vals.p, n, 2 * idx->k, st));
 
-  // runs of equal keys
-  DBuf<uint32_t> head;
-  DBuf<uint64_t> run_excl;
-  GOD_TRY(head.alloc(n, st));
-  GOD_TRY(run_excl.alloc(n + 1, st));
-  if (n) GOD_LAUNCH(mark_heads, g, kThreads, 0, st, keys.p, n, head.p);
-  GOD_TRY(exclusive_scan_u32(head.p, run_excl.p, n, st));
-  uint64_t n_runs = 0;
-  GOD_CK(cudaMemcpyAsync(&n_runs, run_excl.p + n, 8, cudaMemcpyDeviceToHost, st));
+  // runs of equal keys, the filter, and the output arrays
+  DBuf<uint64_t> rv, roff;
+  GOD_TRY(rv.alloc(n, st));
+  GOD_TRY(roff.alloc(n + 1, st));
+  if (n) GOD_LAUNCH(run_heads, g, kThreads, 0, st, keys.p, n, idx->max_occ, rv.p);
+  GOD_TRY(exclusive_scan_u64(rv.p, roff.p, n, st));
+  uint64_t tot = 0;
+  GOD_CK(cudaMemcpyAsync(&tot, roff.p + n, 8, cudaMemcpyDeviceToHost, st));
   GOD_CK(cudaStreamSynchronize(st));
-  DBuf<uint64_t> run_start, kept_len, kept_rank, ent_off;
-  DBuf<uint32_t> kept;
-  GOD_TRY(run_start.alloc(n_runs + 1, st));
-  GOD_TRY(kept.alloc(n_runs, st));
-  GOD_TRY(kept_len.alloc(n_runs, st));
-  GOD_TRY(kept_rank.alloc(n_runs + 1, st));
-  GOD_TRY(ent_off.alloc(n_runs + 1, st));
-  const unsigned gr = std::min<unsigned>(blocks_for(n_runs), (unsigned)num_sms() * 32);
-  GOD_LAUNCH(run_starts, g, kThreads, 0, st, head.p, run_excl.p, n, run_start.p, n_runs);
-  if (n_runs) GOD_LAUNCH(run_keep, gr, kThreads, 0, st, run_start.p, n_runs, idx->max_occ, kept.p, kept_len.p);
-  GOD_TRY(exclusive_scan_u32(kept.p, kept_rank.p, n_runs, st));
-  GOD_TRY(exclusive_scan_u64(kept_len.p, ent_off.p, n_runs, st));
-  uint64_t sizes[2] = {0, 0};
-  GOD_CK(cudaMemcpyAsync(&sizes[0], kept_rank.p + n_runs, 8, cudaMemcpyDeviceToHost, st));
-  GOD_CK(cudaMemcpyAsync(&sizes[1], ent_off.p + n_runs, 8, cudaMemcpyDeviceToHost, st));
-  GOD_CK(cudaStreamSynchronize(st));
-  const uint64_t U = sizes[0], E = sizes[1];
-  if (E >= (1ULL << 32)) {
-    set_error("index: more than 2^32 entries");
-    return GOD_EINVAL;
+  if (tot == ~0ULL) {
+    set_error("index: prefix-sum wait gave up");
+    return GOD_ETIMEOUT;
   }
+  const uint64_t U = tot >> 32, E = tot & 0xFFFFFFFFULL;
   DBuf<uint64_t> okeys, oent;
   DBuf<uint32_t> ostart;
   GOD_TRY(okeys.alloc(U, st));
   GOD_TRY(ostart.alloc(U + 1, st));
   GOD_TRY(oent.alloc(E, st));
-  GOD_LAUNCH(emit_keys, gr, kThreads, 0, st, keys.p, run_start.p, kept.p, kept_rank.p, ent_off.p, n_runs, okeys.p,
-             ostart.p);
-  if (n) GOD_LAUNCH(emit_entries, g, kThreads, 0, st, vals.p, run_excl.p, run_start.p, kept.p, ent_off.p, n, oent.p);
-
-  // hash table at load <= 1/2
-  uint64_t cap_ht = 16;
-  while (cap_ht < 2 * U) cap_ht <<= 1;
-  DBuf<ulonglong2> ht;
-  GOD_TRY(ht.alloc(cap_ht, st));
-  GOD_CK(cudaMemsetAsync(ht.p, 0xFF, cap_ht * sizeof(ulonglong2), st));
-  if (U) GOD_LAUNCH(ht_insert, std::min<unsigned>(blocks_for(U), (unsigned)num_sms() * 32), kThreads, 0, st,
-                    okeys.p, ostart.p, U, ht.p, cap_ht - 1);
-  GOD_CK(cudaStreamSynchronize(st));
+  if (n) {
+    GOD_LAUNCH(emit_runs, g, kThreads, 0, st, keys.p, vals.p, n, rv.p, roff.p, okeys.p, ostart.p, oent.p);
+  } else {
+    GOD_CK(cudaMemsetAsync(ostart.p, 0, sizeof(uint32_t), st));
+  }
+  // hash table at load <= 1/2; the slot word splits 64 bits into the quotient
+  // (2k - lc bits), the rank (rb bits) and the displacement (the rest, >= 9
+  // bits for k <= 28 since 2^lc >= 2U)
+  uint32_t rb = 1;
+  while (rb < 63 && (1ULL << rb) < U) ++rb;
+  uint32_t lc = 4;
+  while ((1ULL << lc) < 2 * U) ++lc;
+  DBuf<uint64_t> ht;
+  DBuf<int> ovf;
+  GOD_TRY(ovf.alloc(1, st));
+  for (;; ++lc) {
+    const uint32_t qb = 2 * idx->k > (int)lc ? 2 * idx->k - lc : 0;
+    const uint32_t db = 64 - qb - rb;
+    if (qb + rb > 62 || lc > 40) {
+      set_error("index: hash table does not fit");
+      return GOD_EINVAL;
+    }
+    const uint64_t cap = 1ULL << lc;
+    GOD_TRY(ht.alloc(cap, st));
+    GOD_CK(cudaMemsetAsync(ht.p, 0xFF, cap * sizeof(uint64_t), st));
+    GOD_CK(cudaMemsetAsync(ovf.p, 0, sizeof(int), st));
+    if (U) GOD_LAUNCH(ht_insert, std::min<unsigned>(blocks_for(U), (unsigned)num_sms() * 32), kThreads, 0, st,
+                      okeys.p, U, ht.p, lc, db, rb, ovf.p);
+    int h_ovf = 0;
+    GOD_CK(cudaMemcpyAsync(&h_ovf, ovf.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    GOD_CK(cudaStreamSynchronize(st));
+    if (!h_ovf) {
+      idx->ht_lc = lc;
+      idx->ht_db = db;
+      idx->ht_rb = rb;
+      idx->ht_cap = cap;
+      break;
+    }
+    ht.release();
+  }
   idx->n_keys = U;
   idx->n_ent = E;
   idx->d_keys = okeys.take();
   idx->d_start = ostart.take();
   idx->d_ent = oent.take();
   idx->d_ht = ht.take();
-  idx->ht_cap = cap_ht;
-  idx->device_bytes = U * 8 + (U + 1) * 4 + E * 8 + cap_ht * 16;
+  idx->device_bytes = U * 8 + (U + 1) * 4 + E * 8 + idx->ht_cap * 8;
   return GOD_OK;
 }
 

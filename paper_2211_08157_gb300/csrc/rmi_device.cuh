@@ -34,24 +34,36 @@ __device__ __forceinline__ int64_t rmi_leaf_pred(float slope, float icept, uint6
   return (int64_t)floorf(v);
 }
 
-// Open-addressing probe: start | count << 32 of key, 0 when absent.
-__device__ __forceinline__ uint64_t ht_find(const ulonglong2* __restrict__ ht, uint64_t mask, uint64_t key) {
-  uint64_t slot = key & mask;
-  for (uint64_t probe = 0; probe <= mask; ++probe) {
-    const ulonglong2 e = __ldg(ht + slot);
-    if (e.x == key) return e.y;
-    if (e.x == kEmptyKey) return 0;
-    slot = (slot + 1) & mask;
+// Open-addressing probe: start | count << 32 of key, 0 when absent. Linear
+// probing from the home slot key mod 2^lc; a slot holds the key's quotient
+// key >> lc, its displacement d from the home slot and its rank in keys[]. The
+// home slot is implied by the probe position, so (quotient, d) identifies the
+// whole key and a match is exact.
+__device__ __forceinline__ uint64_t ht_find(const DeviceIndex& di, uint64_t key) {
+  const uint32_t lc = di.ht_lc, db = di.ht_db, rb = di.ht_rb;
+  const uint64_t mask = (1ULL << lc) - 1, h = key & mask;
+  const uint64_t q = key >> lc;
+  const uint32_t qb = 64 - db - rb;            // quotient bits: keys below 2^(lc + qb) only
+  if (lc + qb < 64 && (q >> qb) != 0) return 0;
+  const uint64_t maxd = (1ULL << db) - 2;
+  for (uint64_t d = 0; d <= maxd; ++d) {
+    const uint64_t w = __ldg(di.ht + ((h + d) & mask));
+    if (w == kEmptyKey) return 0;
+    if ((w >> rb) == ((q << db) | d)) {
+      const uint64_t r = w & ((1ULL << rb) - 1);
+      const uint32_t s = __ldg(di.start + r), e = __ldg(di.start + r + 1);
+      return (uint64_t)s | ((uint64_t)(e - s) << 32);
+    }
   }
   return 0;
 }
 
 __device__ __forceinline__ uint64_t rmi_find(const DeviceIndex& di, const RmiRoot& R, uint64_t key) {
-  if (key < R.kmin || key > R.kmax) return ht_find(di.ht, di.ht_mask, key);
+  if (key < R.kmin || key > R.kmax) return ht_find(di, key);
   const uint32_t leaf = rmi_root_leaf(R, key);
   const RmiLeaf L = di.leaves[leaf];
   const uint32_t eps = (uint32_t)(L.base_eps >> 56);
-  if (eps > di.eps_max) return ht_find(di.ht, di.ht_mask, key);
+  if (eps > di.eps_max) return ht_find(di, key);
   const int64_t pred = rmi_leaf_pred(L.slope, L.icept, L.base_eps & ((1ULL << 56) - 1), key);
   int64_t lo = pred - (int64_t)eps, hi = pred + (int64_t)eps;
   if (lo < 0) lo = 0;

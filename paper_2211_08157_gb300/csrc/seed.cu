@@ -16,8 +16,9 @@
 //  * Every seeding minimizer whose key is kept in the index yields one anchor
 //    per index entry; anchors are counted per read, offsets scanned, and each
 //    read's anchors are produced and sorted in on-chip memory in one step
-//    (a warp per read for short lists, a CTA per read with chunked bitonic
-//    sorts and merge-path passes for long ones).
+//    (a thread per read for lists of at most 16, a warp per read for short
+//    lists, a CTA per read with chunked bitonic sorts and merge-path passes for
+//    long ones).
 #include <algorithm>
 #include <vector>
 
@@ -40,7 +41,7 @@ inline unsigned grid_for(uint64_t n, int per = kT, unsigned cap_mult = 32) {
 }
 
 struct RecSet {
-  const MinRec* rec;
+  const uint32_t* pz;       // (read position << 1) | z of each record
   const uint64_t* sc;       // lookup result: start | count << 32
   const uint64_t* seg_off;  // first record of each segment
   const uint32_t* seg_cnt;  // records of each segment
@@ -224,7 +225,7 @@ __device__ __forceinline__ void store_anchor(god_anchor* out, uint32_t read, uin
   v.y = (uint32_t)(key >> 1) & 0x7FFFFFFFu;
   v.z = (uint32_t)(key >> 32);
   v.w = (uint32_t)(key & 1u);
-  *reinterpret_cast<uint4*>(out) = v;
+  __stcs(reinterpret_cast<uint4*>(out), v);   // streamed: keep the index entries in L2
 }
 
 // Tiny anchor lists (<= 16): one thread per read gathers them into registers
@@ -256,10 +257,10 @@ __global__ void __launch_bounds__(kT) fill_sort_tiny(RecSets sets, const uint32_
       const uint64_t sc = S.sc[beg + r];
       const uint32_t c = (uint32_t)(sc >> 32);
       if (!c) continue;
-      const MinRec m = S.rec[beg + r];
+      const uint32_t pzv = S.pz[beg + r];
       const uint32_t start = (uint32_t)sc;
       for (uint32_t e = 0; e < c; ++e, ++fill) {
-        const uint64_t key = anchor_key(__ldg(ent + start + e), m.pos, m.segz & 1u);
+        const uint64_t key = anchor_key(__ldg(ent + start + e), pzv >> 1, pzv & 1u);
 #pragma unroll
         for (int q = 0; q < kTinyCap; ++q) v[q] = (q == (int)fill) ? key : v[q];
       }
@@ -309,9 +310,9 @@ __global__ void __launch_bounds__(kT) fill_sort_small(RecSets sets, const uint32
         c = (uint32_t)(sc >> 32);
         start = (uint32_t)sc;
         if (c) {
-          const MinRec m = S.rec[beg + r];
-          pos = m.pos;
-          z = m.segz & 1u;
+          const uint32_t pzv = S.pz[beg + r];
+          pos = pzv >> 1;
+          z = pzv & 1u;
         }
       }
       uint32_t incl = c;
@@ -378,9 +379,9 @@ __device__ void fill_range(const RecSet& S, uint64_t beg, uint32_t cnt, const ui
       const uint64_t e_lo = a0 < lo ? lo - a0 : 0;
       const uint64_t e_hi = a0 + c > hi ? (hi > a0 ? hi - a0 : 0) : c;
       if (e_lo < e_hi) {
-        const MinRec m = S.rec[beg + r];
-        pos = m.pos;
-        z = m.segz & 1u;
+        const uint32_t pzv = S.pz[beg + r];
+        pos = pzv >> 1;
+        z = pzv & 1u;
         for (uint64_t e = e_lo; e < e_hi; ++e) dst[a0 + e - lo] = anchor_key(__ldg(ent + start + e), pos, z);
       }
     }
@@ -481,13 +482,14 @@ __global__ void __launch_bounds__(kLargeThreads) fill_sort_large(RecSets sets, c
   }
 }
 
-// Staged sketch output -> ordered records, each looked up in the index on
-// the way (warp per sketch sub-tile; the lookup result is start | count << 32).
+// Staged sketch output -> ordered per-record (position << 1 | z) words and
+// index lookups (warp per sketch sub-tile; a lookup result is start | count
+// << 32). The key is not kept: nothing after the lookup needs it.
 template <int VIA>
 __global__ void __launch_bounds__(kT) compact_lookup(const MinRec* __restrict__ staging,
                                                      const uint32_t* __restrict__ sub_cnt,
                                                      const uint64_t* __restrict__ sub_off, uint64_t n_sub, int WT,
-                                                     DeviceIndex di, MinRec* __restrict__ out,
+                                                     DeviceIndex di, uint32_t* __restrict__ pz,
                                                      uint64_t* __restrict__ sc) {
   __shared__ RmiRoot R;
   if (VIA == 1) {
@@ -501,9 +503,10 @@ __global__ void __launch_bounds__(kT) compact_lookup(const MinRec* __restrict__ 
     const uint64_t o = sub_off[sub];
     const MinRec* src = staging + sub * (uint64_t)WT;
     for (uint32_t i = lane; i < c; i += 32) {
-      const MinRec r = src[i];
-      out[o + i] = r;
-      sc[o + i] = VIA == 1 ? rmi_find(di, R, r.key) : ht_find(di.ht, di.ht_mask, r.key);
+      const uint4 r = __ldcs(reinterpret_cast<const uint4*>(src + i));   // read once
+      const uint64_t key = ((uint64_t)r.y << 32) | r.x;
+      pz[o + i] = (r.z << 1) | (r.w & 1u);
+      sc[o + i] = VIA == 1 ? rmi_find(di, R, key) : ht_find(di, key);
     }
   }
 }
@@ -513,12 +516,12 @@ struct SetBufs {
   DBuf<SegDesc> segs;
   DBuf<uint32_t> vlen;
   DBuf<uint64_t> voff;
-  DBuf<MinRec> rec;
+  DBuf<uint32_t> pz;
   DBuf<uint64_t> sc;
   DBuf<uint32_t> seg_cnt;
   DBuf<uint64_t> seg_off;
   uint64_t n_seg = 0, n_rec = 0;
-  RecSet view() const { return RecSet{rec.p, sc.p, seg_off.p, seg_cnt.p}; }
+  RecSet view() const { return RecSet{pz.p, sc.p, seg_off.p, seg_cnt.p}; }
 };
 
 // err (optional, device int) is read back together with the stream length;
@@ -552,19 +555,20 @@ int sketch_and_lookup(const god_index* idx, const uint8_t* d_reads, SetBufs& B, 
   StagedSketch SS;
   GOD_TRY(run_sketch_staged(job, st, SS, nullptr));
   B.n_rec = SS.total;
-  GOD_TRY(B.rec.alloc(SS.total, st));
+  GOD_TRY(B.pz.alloc(SS.total, st));
   GOD_TRY(B.sc.alloc(SS.total, st));
   if (SS.total) {
     const DeviceIndex di = device_view(idx, via);
     const unsigned blocks = (unsigned)std::min<uint64_t>((SS.n_sub * 32 + kT - 1) / kT, (uint64_t)num_sms() * 16);
     if (via == 1 && di.leaves)
       GOD_LAUNCH(compact_lookup<1>, blocks, kT, 0, st, SS.staging.p, SS.sub_cnt.p, SS.sub_off.p, SS.n_sub, SS.WT,
-                 di, B.rec.p, B.sc.p);
+                 di, B.pz.p, B.sc.p);
     else
       GOD_LAUNCH(compact_lookup<0>, blocks, kT, 0, st, SS.staging.p, SS.sub_cnt.p, SS.sub_off.p, SS.n_sub, SS.WT,
-                 di, B.rec.p, B.sc.p);
-    // algorithmic bytes: record read + written (16 + 16), probe >= 32, result 8
-    prof_add_work(via == 1 && di.leaves ? "compact_lookup<1>" : "compact_lookup<0>", 72.0 * (double)SS.total,
+                 di, B.pz.p, B.sc.p);
+    // algorithmic bytes: record read 16, position word 4, result 8, one table
+    // slot 8 and the key's two offsets 8
+    prof_add_work(via == 1 && di.leaves ? "compact_lookup<1>" : "compact_lookup<0>", 44.0 * (double)SS.total,
                   (double)SS.total);
   }
   GOD_TRY(B.seg_off.alloc(B.n_seg + 1, st));
