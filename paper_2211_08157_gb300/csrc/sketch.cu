@@ -70,11 +70,19 @@ __device__ __forceinline__ uint64_t xorshr64(uint64_t x) {
 // multiplications by constants: ~x + (x << 21) = x * (2^21 - 1) - 1,
 // x + (x << 3) + (x << 8) = 265 x, x + (x << 2) + (x << 4) = 21 x and
 // x + (x << 31) = (2^31 + 1) x (mod 2^64), so each is one 64 x 32-bit
-// multiply-add. WIDE (2k > 32): the mask only touches the high half. Otherwise
-// the same steps in 32-bit arithmetic give the identical value.
-template <bool WIDE>
+// multiply-add. HM (hash mode) 2: 2k > 32, the mask only touches the high
+// half; HM 1: 32 < 2k <= 46, the high half has at most 14 bits, so every
+// right shift (by 14, 24 or 28) leaves it zero and only the low half changes.
+// HM 0: the same steps in 32-bit arithmetic give the identical value.
+template <int S>
+__device__ __forceinline__ uint64_t xorshr64_narrow(uint64_t x) {
+  const uint32_t lo = (uint32_t)x, hi = (uint32_t)(x >> 32);
+  return ((uint64_t)hi << 32) | (lo ^ __funnelshift_r(lo, hi, S));
+}
+
+template <int HM>
 __device__ __forceinline__ uint64_t wang_mix(uint64_t key, uint64_t mask) {
-  if (WIDE) {
+  if (HM == 2) {
     uint64_t x = key;
     x = mad_c64(x, 0x1FFFFFu, ~0ULL) & mask;
     x = xorshr64<24>(x);
@@ -82,6 +90,16 @@ __device__ __forceinline__ uint64_t wang_mix(uint64_t key, uint64_t mask) {
     x = xorshr64<14>(x);
     x = mad_c64(x, 21u, 0) & mask;
     x = xorshr64<28>(x);
+    x = mad_c64(x, 0x80000001u, 0) & mask;
+    return x;
+  } else if (HM == 1) {
+    uint64_t x = key;
+    x = mad_c64(x, 0x1FFFFFu, ~0ULL) & mask;
+    x = xorshr64_narrow<24>(x);
+    x = mad_c64(x, 265u, 0) & mask;
+    x = xorshr64_narrow<14>(x);
+    x = mad_c64(x, 21u, 0) & mask;
+    x = xorshr64_narrow<28>(x);
     x = mad_c64(x, 0x80000001u, 0) & mask;
     return x;
   } else {
@@ -167,10 +185,10 @@ __host__ __device__ inline int sub_tile_for(int warps, int k, int w, int chunks 
 
 // Window stage of the kernel, by variant WV: blocks of exactly WV keys in
 // registers (WV > 0: the window lengths of the standard presets, w = 11 and 19
-// for k > 16 and w = 10 for k <= 15), blocks of up to -WV keys (WV = -12 or
-// -20), or shared-memory passes for any w (WV = 0).
+// for 16 < k <= 23 and w = 10 for k <= 15), blocks of up to -WV keys (WV = -12
+// or -20), or shared-memory passes for any w (WV = 0).
 __host__ __device__ inline int window_variant(int k, int w) {
-  if (k > 16 && (w == 11 || w == 19)) return w;
+  if (k > 16 && k <= 23 && (w == 11 || w == 19)) return w;
   if (k <= 15 && w == 10) return w;
   return w <= 12 ? -12 : w <= 20 ? -20 : 0;
 }
@@ -436,7 +454,7 @@ __device__ __forceinline__ void count_segments(uint32_t* seg_cnt, uint32_t g, in
 // compaction pass order them; tiles are strided over CTAs). Otherwise:
 // directly to their final place, found by a decoupled look-back over
 // sub-tiles taken from a ticket.
-template <int WARPS, typename KT, bool WIDE, bool STAGED, int WV>
+template <int WARPS, typename KT, int HM, bool STAGED, int WV>
 __global__ void __launch_bounds__(WARPS * 32) sketch_kernel(const __grid_constant__ SketchArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int BLOCK = WARPS * 32;
@@ -628,7 +646,7 @@ __global__ void __launch_bounds__(WARPS * 32) sketch_kernel(const __grid_constan
           KT kk = 0;
           if (((nn >> j) & (uint32_t)nmask) == 0) {
             uint64_t fwd, rev;
-            if (WIDE) {     // 2k > 32: every shift below is under 32
+            if (HM > 0) {   // 2k > 32: every shift below is under 32
               const uint32_t sh = top_shift - 2 * j;
               const uint32_t th = (uint32_t)(tb >> 32);
               fwd = ((uint64_t)((th >> sh) & (uint32_t)(mask >> 32)) << 32) | __funnelshift_r((uint32_t)tb, th, sh);
@@ -638,12 +656,12 @@ __global__ void __launch_bounds__(WARPS * 32) sketch_kernel(const __grid_constan
               fwd = (uint32_t)(tb >> (top_shift - 2 * j)) & (uint32_t)mask;
               rev = (uint32_t)(tl >> (2 * j)) & (uint32_t)mask;
             }
-            if (fwd == rev) {
+            if (!(k & 1) && fwd == rev) {   // a palindrome needs even k
               kk = PALIN;
             } else {
               const bool z = rev < fwd;
               zq |= (uint32_t)z << (8 * j);
-              kk = (KT)(wang_mix<WIDE>(z ? rev : fwd, mask) + 1);
+              kk = (KT)(wang_mix<HM>(z ? rev : fwd, mask) + 1);
               valid4 |= 1u << j;
             }
           }
@@ -752,9 +770,9 @@ __global__ void __launch_bounds__(WARPS * 32) sketch_kernel(const __grid_constan
   }
 }
 
-template <int WARPS, typename KT, bool WIDE, bool STAGED, int WV>
+template <int WARPS, typename KT, int HM, bool STAGED, int WV>
 int launch_sketch_mw(const SketchArgs& a, cudaStream_t st) {
-  auto sketch = sketch_kernel<WARPS, KT, WIDE, STAGED, WV>;
+  auto sketch = sketch_kernel<WARPS, KT, HM, STAGED, WV>;
   const size_t smem = tile_layout(WARPS, a.T, a.job.k, a.job.w, (int)sizeof(KT), window_regs(WV)).bytes;
   GOD_CK(cudaFuncSetAttribute(sketch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
@@ -770,26 +788,27 @@ int launch_sketch_mw(const SketchArgs& a, cudaStream_t st) {
   return GOD_OK;
 }
 
-template <int WARPS, typename KT, bool WIDE, bool STAGED>
+template <int WARPS, typename KT, int HM, bool STAGED>
 int launch_sketch_kt(const SketchArgs& a, cudaStream_t st) {
   const int wv = window_variant(a.job.k, a.job.w);
-  if constexpr (WIDE) {
-    if (wv == 11) return launch_sketch_mw<WARPS, KT, WIDE, STAGED, 11>(a, st);
-    if (wv == 19) return launch_sketch_mw<WARPS, KT, WIDE, STAGED, 19>(a, st);
+  if constexpr (HM == 1) {
+    if (wv == 11) return launch_sketch_mw<WARPS, KT, HM, STAGED, 11>(a, st);
+    if (wv == 19) return launch_sketch_mw<WARPS, KT, HM, STAGED, 19>(a, st);
   }
   if constexpr (sizeof(KT) == 4) {
-    if (wv == 10) return launch_sketch_mw<WARPS, KT, WIDE, STAGED, 10>(a, st);
+    if (wv == 10) return launch_sketch_mw<WARPS, KT, HM, STAGED, 10>(a, st);
   }
-  if (wv == -12) return launch_sketch_mw<WARPS, KT, WIDE, STAGED, -12>(a, st);
-  if (wv == -20) return launch_sketch_mw<WARPS, KT, WIDE, STAGED, -20>(a, st);
-  return launch_sketch_mw<WARPS, KT, WIDE, STAGED, 0>(a, st);
+  if (wv == -12) return launch_sketch_mw<WARPS, KT, HM, STAGED, -12>(a, st);
+  if (wv == -20) return launch_sketch_mw<WARPS, KT, HM, STAGED, -20>(a, st);
+  return launch_sketch_mw<WARPS, KT, HM, STAGED, 0>(a, st);
 }
 
 template <int WARPS, bool STAGED>
 int launch_sketch_w(const SketchArgs& a, cudaStream_t st) {
-  if (a.job.k > 16) return launch_sketch_kt<WARPS, uint64_t, true, STAGED>(a, st);
-  if (a.job.k <= 15) return launch_sketch_kt<WARPS, uint32_t, false, STAGED>(a, st);
-  return launch_sketch_kt<WARPS, uint64_t, false, STAGED>(a, st);
+  if (a.job.k > 23) return launch_sketch_kt<WARPS, uint64_t, 2, STAGED>(a, st);
+  if (a.job.k > 16) return launch_sketch_kt<WARPS, uint64_t, 1, STAGED>(a, st);
+  if (a.job.k <= 15) return launch_sketch_kt<WARPS, uint32_t, 0, STAGED>(a, st);
+  return launch_sketch_kt<WARPS, uint64_t, 0, STAGED>(a, st);
 }
 
 // First segment of every CTA tile (the segment holding its first halo base).

@@ -55,6 +55,8 @@ SKETCH_CASES = [
     (33_333, "1", 0, 16, 5, 0.001), (12_345, "1000101001", 3, 12, 7, 0.0), (9_999, "01", 0, 8, 4, 0.02),
     (40_000, "1110", 1, 28, 40, 0.0), (4_321, "1", 0, 1, 1, 0.01), (7_777, "10", 0, 4, 3, 0.0),
     (100_000, "10", 0, 15, 10, 0.0005), (2_500, "1", 0, 11, 255, 0.0), (3_000, "11", 1, 2, 2, 0.0),
+    # hash-width boundaries (2k = 34, 46, 50) with register window stages
+    (15_000, "1", 0, 17, 12, 0.0), (20_000, "110", 0, 23, 19, 0.001), (30_000, "10", 0, 25, 11, 0.001),
 ]
 
 
