@@ -576,30 +576,66 @@ __global__ void __launch_bounds__(WARPS * 32) sketch_kernel(const __grid_constan
           }
           if (n8 && (d0.flags & kSegCapped) && J.read_flag) J.read_flag[d0.read] = 1u;
         } else {
-          SegDesc d = d0;
-          uint64_t gend = J.seg_voff[g + 1];
-          const uint8_t* src = J.bytes + d.byte_off + d.shift;
-#pragma unroll
-          for (int dd = 0; dd < 8; ++dd) {
-            const int64_t v = v0 + dd;
-            uint32_t e = 4;
-            if (v >= 0 && (uint64_t)v < J.V && 8 * c + dd < n_codes) {
-              if ((uint64_t)v >= gend) {
-                ++g;
-                d = J.segs[g];
-                src = J.bytes + d.byte_off + d.shift;
-                gend = J.seg_voff[g + 1];
-                j = 0; q = 0; r = 0;
-              }
-              if (j < d.m) {
-                e = s_lut[__ldg(src + (uint64_t)p * q + s_off[r])];
-                if (e == 4 && (d.flags & kSegCapped) && J.read_flag) J.read_flag[d.read] = 1u;
-              }
-              ++j;
-              if (++r == (uint32_t)x) { r = 0; ++q; }
+          // the chunk reaches the end of segment g: rem bases of g, its
+          // separator, then bases of segment g + 1 (when all of them are
+          // bases of g + 1, the two are walked side by side without branches)
+          const uint32_t rem = d0.m - j;   // < 8 here
+          bool two = false;
+          SegDesc d1 = d0;
+          if (v0 >= 0 && 8 * c + 8 <= n_codes) {
+            if (rem == 7) {
+              two = true;
+            } else if (g + 1 < J.n_seg) {
+              d1 = J.segs[g + 1];
+              two = 6 - rem < d1.m;
             }
-            f16 |= (e & 3u) << (14 - 2 * dd);
-            n8 |= (e >> 2) << dd;
+          }
+          if (two) {
+            const uint8_t* s0 = J.bytes + d0.byte_off + d0.shift;
+            const uint8_t* s1 = J.bytes + d1.byte_off + d1.shift;
+            uint32_t o0 = (uint32_t)p * q + s_off[r], r0 = r;
+            uint32_t o1 = s_off[0], r1 = 0;
+#pragma unroll
+            for (int dd = 0; dd < 8; ++dd) {
+              const bool in0 = dd < (int)rem, in1 = dd > (int)rem;
+              const uint32_t b = __ldg((in0 ? s0 + o0 : s1 + o1));   // the separator reads a real base, unused
+              const uint32_t e = (in0 || in1) ? s_lut[b] : 4u;
+              f16 |= (e & 3u) << (14 - 2 * dd);
+              n8 |= (e >> 2) << dd;
+              const uint32_t t0 = s_delta[r0], t1 = s_delta[r1];
+              if (in0) { o0 += t0; r0 = r0 + 1 == (uint32_t)x ? 0 : r0 + 1; }
+              if (in1) { o1 += t1; r1 = r1 + 1 == (uint32_t)x ? 0 : r1 + 1; }
+            }
+            if (J.read_flag) {   // an N in a capped segment marks its read
+              if ((n8 & ((1u << rem) - 1u)) && (d0.flags & kSegCapped)) J.read_flag[d0.read] = 1u;
+              if (rem < 7 && (n8 >> (rem + 1)) && (d1.flags & kSegCapped)) J.read_flag[d1.read] = 1u;
+            }
+          } else {
+            SegDesc d = d0;
+            uint64_t gend = J.seg_voff[g + 1];
+            const uint8_t* src = J.bytes + d.byte_off + d.shift;
+#pragma unroll
+            for (int dd = 0; dd < 8; ++dd) {
+              const int64_t v = v0 + dd;
+              uint32_t e = 4;
+              if (v >= 0 && (uint64_t)v < J.V && 8 * c + dd < n_codes) {
+                if ((uint64_t)v >= gend) {
+                  ++g;
+                  d = J.segs[g];
+                  src = J.bytes + d.byte_off + d.shift;
+                  gend = J.seg_voff[g + 1];
+                  j = 0; q = 0; r = 0;
+                }
+                if (j < d.m) {
+                  e = s_lut[__ldg(src + (uint64_t)p * q + s_off[r])];
+                  if (e == 4 && (d.flags & kSegCapped) && J.read_flag) J.read_flag[d.read] = 1u;
+                }
+                ++j;
+                if (++r == (uint32_t)x) { r = 0; ++q; }
+              }
+              f16 |= (e & 3u) << (14 - 2 * dd);
+              n8 |= (e >> 2) << dd;
+            }
           }
         }
       }
