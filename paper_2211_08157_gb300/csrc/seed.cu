@@ -502,11 +502,50 @@ __global__ void __launch_bounds__(kT) compact_lookup(const MinRec* __restrict__ 
     const uint32_t c = sub_cnt[sub];
     const uint64_t o = sub_off[sub];
     const MinRec* src = staging + sub * (uint64_t)WT;
-    for (uint32_t i = lane; i < c; i += 32) {
-      const uint4 r = __ldcs(reinterpret_cast<const uint4*>(src + i));   // read once
-      const uint64_t key = ((uint64_t)r.y << 32) | r.x;
-      pz[o + i] = (r.z << 1) | (r.w & 1u);
-      sc[o + i] = VIA == 1 ? rmi_find(di, R, key) : ht_find(di, key);
+    // two records per lane, each dependent step issued for both first (more in
+    // flight per lane measured slower)
+    constexpr int U = 2;
+    for (uint32_t i0 = lane; i0 < c; i0 += 32 * U) {
+      uint64_t key[U], rk[U];
+      uint32_t pzv[U];
+      bool ok[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const uint32_t i = i0 + 32 * u;
+        ok[u] = i < c;
+        uint4 r = make_uint4(0, 0, 0, 0);
+        if (ok[u]) r = __ldcs(reinterpret_cast<const uint4*>(src + i));   // read once
+        key[u] = ((uint64_t)r.y << 32) | r.x;
+        pzv[u] = (r.z << 1) | (r.w & 1u);
+      }
+      if (VIA == 1) {
+        RmiLeaf L[U];
+        bool hashed[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          hashed[u] = !rmi_in_range(R, key[u]);
+          L[u] = ok[u] && !hashed[u] ? di.leaves[rmi_root_leaf(R, key[u])] : RmiLeaf{0, 0.0f, 0.0f};
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          hashed[u] = hashed[u] || (uint32_t)(L[u].base_eps >> 56) > di.eps_max;
+          rk[u] = !ok[u] ? kNoRank : hashed[u] ? ht_rank(di, key[u], ht_home_word(di, key[u]))
+                                                 : rmi_rank_in_leaf(di, L[u], key[u]);
+        }
+      } else {
+        uint64_t w[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) w[u] = ok[u] ? ht_home_word(di, key[u]) : kEmptyKey;
+#pragma unroll
+        for (int u = 0; u < U; ++u) rk[u] = ok[u] ? ht_rank(di, key[u], w[u]) : kNoRank;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (ok[u]) {
+          pz[o + i0 + 32 * u] = pzv[u];
+          sc[o + i0 + 32 * u] = rank_payload(di, rk[u]);
+        }
+      }
     }
   }
 }
