@@ -24,11 +24,22 @@ inline unsigned blocks_for(uint64_t n, int per = kThreads) {
   return (unsigned)std::min<uint64_t>(std::max<uint64_t>(b, 1), 1u << 30);
 }
 
-__global__ void split_records(const MinRec* rec, uint64_t n, uint64_t* keys, uint64_t* vals) {
-  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-    const MinRec r = rec[i];
-    keys[i] = r.key;
-    vals[i] = ((uint64_t)r.pos << 1) | (r.segz & 1u);
+// Staged sketch records of each warp sub-tile -> keys[] and vals[] =
+// (pos << 1) | z at their ordered place (warp per sub-tile).
+__global__ void split_staged(const MinRec* __restrict__ staging, const uint32_t* __restrict__ sub_cnt,
+                             const uint64_t* __restrict__ sub_off, uint64_t n_sub, int WT, uint64_t* __restrict__ keys,
+                             uint64_t* __restrict__ vals) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x / 32);
+  for (uint64_t sub = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) / 32; sub < n_sub; sub += warps) {
+    const uint32_t c = sub_cnt[sub];
+    const uint64_t o = sub_off[sub];
+    const MinRec* src = staging + sub * (uint64_t)WT;
+    for (uint32_t i = lane; i < c; i += 32) {
+      const uint4 r = __ldcs(reinterpret_cast<const uint4*>(src + i));   // read once
+      keys[o + i] = ((uint64_t)r.y << 32) | r.x;
+      vals[o + i] = ((uint64_t)r.z << 1) | (r.w & 1u);
+    }
   }
 }
 
@@ -174,18 +185,21 @@ int build_index_device(god_index* idx, const uint8_t* d_ref, uint64_t len, cudaS
   job.w = idx->w;
   job.pat = P;
   job.tune = idx->params.tune;
-  DBuf<MinRec> rec;
-  uint64_t total = 0;
-  GOD_TRY(run_sketch(job, st, rec, &total, nullptr));
-  const uint64_t n = total;
+  StagedSketch S;
+  GOD_TRY(run_sketch_staged(job, st, S, nullptr));
+  const uint64_t n = S.total;
   idx->n_min = n;
 
   DBuf<uint64_t> keys, vals;
   GOD_TRY(keys.alloc(n, st));
   GOD_TRY(vals.alloc(n, st));
   const unsigned g = std::min<unsigned>(blocks_for(n), (unsigned)num_sms() * 32);
-  if (n) GOD_LAUNCH(split_records, g, kThreads, 0, st, rec.p, n, keys.p, vals.p);
-  rec.release();
+  if (n) {
+    const uint64_t blocks = std::min<uint64_t>((S.n_sub * 32 + kThreads - 1) / kThreads, (uint64_t)num_sms() * 16);
+    GOD_LAUNCH(split_staged, (unsigned)blocks, kThreads, 0, st, S.staging.p, S.sub_cnt.p, S.sub_off.p, S.n_sub, S.WT,
+               keys.p, vals.p);
+  }
+  S.staging.release();
   GOD_TRY(radix_sort_pairs(keys.p, vals.p, n, 2 * idx->k, st));
 
   // runs of equal keys, the filter, and the output arrays

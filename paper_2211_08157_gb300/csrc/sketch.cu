@@ -525,13 +525,18 @@ __global__ void __launch_bounds__(WARPS * 32) sketch_kernel(const __grid_constan
       const int64_t v0 = v_first + 8 * (int64_t)c;
       uint32_t f16 = 0, n8 = 0xFFu;
       int2 state = make_int2(-1, 0);
+      // mode 0: all eight are bases of segment g; 1: rem bases of g, its
+      // separator, then bases of g + 1; 2: anything else (stream ends, short
+      // segments); 3: no bases
+      int mode = 3;
+      uint32_t g = 0, j = 0, q = 0, r = 0, rem = 0;
+      SegDesc d0{}, d1{};
       if (act && v0 + 8 > 0 && v0 < (int64_t)J.V && 8 * c < n_codes) {
         n8 = 0;
         const uint64_t vs = v0 < 0 ? 0 : (uint64_t)v0;
         const uint32_t vr = (uint32_t)(vs - base_v);
         // segment of vs: the cached boundaries of the tile's first kBndCache
         // segments (global memory only past them)
-        uint32_t g;
         if (bnd[kBndCache] <= vr && g_tile + kBndCache < J.n_seg) {
           uint32_t lo = g_tile + kBndCache, hi = J.n_seg;
           while (hi - lo > 1) {
@@ -546,97 +551,100 @@ __global__ void __launch_bounds__(WARPS * 32) sketch_kernel(const __grid_constan
             if (bnd[lo + step] <= vr) lo += step;
           g = g_tile + lo;
         }
-        const SegDesc d0 = J.segs[g];
-        uint32_t j = (uint32_t)(vs - J.seg_voff[g]);
+        d0 = J.segs[g];
+        j = (uint32_t)(vs - J.seg_voff[g]);
         // (segment, index of the chunk's first base in it + 8): biased because
         // the stream's first chunk starts before position 0
         state = make_int2((int)g, (int)(j + 8u - (uint32_t)((int64_t)vs - v0)));
-        uint32_t q, r;
         divmod_x(j, (uint32_t)x, xinv, q, r);
-        if (v0 >= 0 && j + 8 <= d0.m && 8 * c + 8 <= n_codes) {
-          // all eight are bases of segment g
-          const uint8_t* src = J.bytes + d0.byte_off + d0.shift;
-          uint32_t o = (uint32_t)p * q + s_off[r];
-          if (x == 1) {
-#pragma unroll
-            for (int dd = 0; dd < 8; ++dd) {
-              const uint32_t e = s_lut[__ldg(src + o + (uint32_t)p * dd)];
-              f16 |= (e & 3u) << (14 - 2 * dd);
-              n8 |= (e >> 2) << dd;
-            }
-          } else {
-#pragma unroll
-            for (int dd = 0; dd < 8; ++dd) {
-              const uint32_t e = s_lut[__ldg(src + o)];
-              f16 |= (e & 3u) << (14 - 2 * dd);
-              n8 |= (e >> 2) << dd;
-              o += s_delta[r];
-              r = r + 1 == (uint32_t)x ? 0 : r + 1;
-            }
+        rem = d0.m - j;
+        d1 = d0;
+        mode = 2;
+        if (v0 >= 0 && 8 * c + 8 <= n_codes) {
+          if (rem >= 7) {
+            mode = rem >= 8 ? 0 : 1;
+          } else if (g + 1 < J.n_seg) {
+            d1 = J.segs[g + 1];
+            if (6 - rem < d1.m) mode = 1;
           }
-          if (n8 && (d0.flags & kSegCapped) && J.read_flag) J.read_flag[d0.read] = 1u;
+        }
+      }
+      const bool warp_single = __all_sync(FULL, mode == 0 || mode == 3);   // every lane, before branching
+      if (mode == 0 && warp_single) {
+        // the whole warp inside single segments
+        const uint8_t* src = J.bytes + d0.byte_off + d0.shift;
+        uint32_t o = (uint32_t)p * q + s_off[r];
+        if (x == 1) {
+#pragma unroll
+          for (int dd = 0; dd < 8; ++dd) {
+            const uint32_t e = s_lut[__ldg(src + o + (uint32_t)p * dd)];
+            f16 |= (e & 3u) << (14 - 2 * dd);
+            n8 |= (e >> 2) << dd;
+          }
         } else {
-          // the chunk reaches the end of segment g: rem bases of g, its
-          // separator, then bases of segment g + 1 (when all of them are
-          // bases of g + 1, the two are walked side by side without branches)
-          const uint32_t rem = d0.m - j;   // < 8 here
-          bool two = false;
-          SegDesc d1 = d0;
-          if (v0 >= 0 && 8 * c + 8 <= n_codes) {
-            if (rem == 7) {
-              two = true;
-            } else if (g + 1 < J.n_seg) {
-              d1 = J.segs[g + 1];
-              two = 6 - rem < d1.m;
-            }
-          }
-          if (two) {
-            const uint8_t* s0 = J.bytes + d0.byte_off + d0.shift;
-            const uint8_t* s1 = J.bytes + d1.byte_off + d1.shift;
-            uint32_t o0 = (uint32_t)p * q + s_off[r], r0 = r;
-            uint32_t o1 = s_off[0], r1 = 0;
 #pragma unroll
-            for (int dd = 0; dd < 8; ++dd) {
-              const bool in0 = dd < (int)rem, in1 = dd > (int)rem;
-              const uint32_t b = __ldg((in0 ? s0 + o0 : s1 + o1));   // the separator reads a real base, unused
-              const uint32_t e = (in0 || in1) ? s_lut[b] : 4u;
-              f16 |= (e & 3u) << (14 - 2 * dd);
-              n8 |= (e >> 2) << dd;
-              const uint32_t t0 = s_delta[r0], t1 = s_delta[r1];
-              if (in0) { o0 += t0; r0 = r0 + 1 == (uint32_t)x ? 0 : r0 + 1; }
-              if (in1) { o1 += t1; r1 = r1 + 1 == (uint32_t)x ? 0 : r1 + 1; }
-            }
-            if (J.read_flag) {   // an N in a capped segment marks its read
-              if ((n8 & ((1u << rem) - 1u)) && (d0.flags & kSegCapped)) J.read_flag[d0.read] = 1u;
-              if (rem < 7 && (n8 >> (rem + 1)) && (d1.flags & kSegCapped)) J.read_flag[d1.read] = 1u;
-            }
+          for (int dd = 0; dd < 8; ++dd) {
+            const uint32_t e = s_lut[__ldg(src + o)];
+            f16 |= (e & 3u) << (14 - 2 * dd);
+            n8 |= (e >> 2) << dd;
+            o += s_delta[r];
+            r = r + 1 == (uint32_t)x ? 0 : r + 1;
+          }
+        }
+        if (n8 && (d0.flags & kSegCapped) && J.read_flag) J.read_flag[d0.read] = 1u;
+      } else if (mode <= 1) {
+        // segments g and g + 1 walked side by side without branches (mode 0
+        // lanes take the same path with every base in g)
+        const uint8_t* s0 = J.bytes + d0.byte_off + d0.shift;
+        const uint8_t* s1 = J.bytes + d1.byte_off + d1.shift;
+        uint32_t o0 = (uint32_t)p * q + s_off[r], r0 = r;
+        uint32_t o1 = s_off[0], r1 = 0;
+#pragma unroll
+        for (int dd = 0; dd < 8; ++dd) {
+          const bool in0 = (uint32_t)dd < rem, in1 = (uint32_t)dd > rem;
+          const uint32_t b = __ldg((in0 ? s0 + o0 : s1 + o1));   // the separator reads a real base, unused
+          const uint32_t e = (in0 || in1) ? s_lut[b] : 4u;
+          f16 |= (e & 3u) << (14 - 2 * dd);
+          n8 |= (e >> 2) << dd;
+          if (x == 1) {
+            o0 += in0 ? (uint32_t)p : 0u;
+            o1 += in1 ? (uint32_t)p : 0u;
           } else {
-            SegDesc d = d0;
-            uint64_t gend = J.seg_voff[g + 1];
-            const uint8_t* src = J.bytes + d.byte_off + d.shift;
-#pragma unroll
-            for (int dd = 0; dd < 8; ++dd) {
-              const int64_t v = v0 + dd;
-              uint32_t e = 4;
-              if (v >= 0 && (uint64_t)v < J.V && 8 * c + dd < n_codes) {
-                if ((uint64_t)v >= gend) {
-                  ++g;
-                  d = J.segs[g];
-                  src = J.bytes + d.byte_off + d.shift;
-                  gend = J.seg_voff[g + 1];
-                  j = 0; q = 0; r = 0;
-                }
-                if (j < d.m) {
-                  e = s_lut[__ldg(src + (uint64_t)p * q + s_off[r])];
-                  if (e == 4 && (d.flags & kSegCapped) && J.read_flag) J.read_flag[d.read] = 1u;
-                }
-                ++j;
-                if (++r == (uint32_t)x) { r = 0; ++q; }
-              }
-              f16 |= (e & 3u) << (14 - 2 * dd);
-              n8 |= (e >> 2) << dd;
-            }
+            const uint32_t t0 = s_delta[r0], t1 = s_delta[r1];
+            if (in0) { o0 += t0; r0 = r0 + 1 == (uint32_t)x ? 0 : r0 + 1; }
+            if (in1) { o1 += t1; r1 = r1 + 1 == (uint32_t)x ? 0 : r1 + 1; }
           }
+        }
+        if (J.read_flag) {   // an N in a capped segment marks its read
+          const uint32_t r8 = rem < 8 ? rem : 8u;
+          if ((n8 & ((1u << r8) - 1u)) && (d0.flags & kSegCapped)) J.read_flag[d0.read] = 1u;
+          if (rem < 7 && (n8 >> (rem + 1)) && (d1.flags & kSegCapped)) J.read_flag[d1.read] = 1u;
+        }
+      } else if (mode == 2) {
+        SegDesc d = d0;
+        uint64_t gend = J.seg_voff[g + 1];
+        const uint8_t* src = J.bytes + d.byte_off + d.shift;
+#pragma unroll
+        for (int dd = 0; dd < 8; ++dd) {
+          const int64_t v = v0 + dd;
+          uint32_t e = 4;
+          if (v >= 0 && (uint64_t)v < J.V && 8 * c + dd < n_codes) {
+            if ((uint64_t)v >= gend) {
+              ++g;
+              d = J.segs[g];
+              src = J.bytes + d.byte_off + d.shift;
+              gend = J.seg_voff[g + 1];
+              j = 0; q = 0; r = 0;
+            }
+            if (j < d.m) {
+              e = s_lut[__ldg(src + (uint64_t)p * q + s_off[r])];
+              if (e == 4 && (d.flags & kSegCapped) && J.read_flag) J.read_flag[d.read] = 1u;
+            }
+            ++j;
+            if (++r == (uint32_t)x) { r = 0; ++q; }
+          }
+          f16 |= (e & 3u) << (14 - 2 * dd);
+          n8 |= (e >> 2) << dd;
         }
       }
       if (act) cst[c] = state;
