@@ -171,6 +171,14 @@ SketchTune default_sketch_tune(int k, int w);
 // Exclusive prefix sum of n values into out (n + 1 entries: out[n] = total).
 int exclusive_scan_u32(const uint32_t* in, uint64_t* out, uint64_t n, cudaStream_t st);
 int exclusive_scan_u64(const uint64_t* in, uint64_t* out, uint64_t n, cudaStream_t st);
+// out[n] is ~0 when a look-back wait gave up; callers read it back with their
+// next synchronisation and report GOD_ETIMEOUT (scan_total_ok).
+constexpr uint64_t kScanPoison = ~0ULL;
+inline int scan_total_ok(uint64_t total, const char* what) {
+  if (total != kScanPoison) return GOD_OK;
+  set_error(std::string(what) + ": prefix-sum wait gave up");
+  return GOD_ETIMEOUT;
+}
 // The same with a caller-provided workspace of scan_ws_words(n) uint64 words
 // (no allocation: usable inside stream capture).
 uint64_t scan_ws_words(uint64_t n);

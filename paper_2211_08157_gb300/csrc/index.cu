@@ -211,10 +211,7 @@ int build_index_device(god_index* idx, const uint8_t* d_ref, uint64_t len, cudaS
   uint64_t tot = 0;
   GOD_CK(cudaMemcpyAsync(&tot, roff.p + n, 8, cudaMemcpyDeviceToHost, st));
   GOD_CK(cudaStreamSynchronize(st));
-  if (tot == ~0ULL) {
-    set_error("index: prefix-sum wait gave up");
-    return GOD_ETIMEOUT;
-  }
+  GOD_TRY(scan_total_ok(tot, "index"));
   const uint64_t U = tot >> 32, E = tot & 0xFFFFFFFFULL;
   DBuf<uint64_t> okeys, oent;
   DBuf<uint32_t> ostart;

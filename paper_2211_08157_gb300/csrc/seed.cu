@@ -578,6 +578,7 @@ int sketch_and_lookup(const god_index* idx, const uint8_t* d_reads, SetBufs& B, 
     set_error("seed: offsets must be non-decreasing and each read < 2^31 bytes");
     return GOD_EINVAL;
   }
+  GOD_TRY(scan_total_ok(V, "seed"));
   GOD_TRY(B.seg_cnt.alloc(B.n_seg, st));
   SketchJob job{};
   job.bytes = d_reads;
@@ -671,8 +672,11 @@ int seed_device(const god_index* idx, const uint8_t* d_reads, const uint64_t* d_
   GOD_LAUNCH(pa_select, grid_for(n), kT, 0, st, n, p, t, PA.segs.p, PA.view(), need_full.p, shift.p, src.p,
              seed_seg.p, read_cnt.p, fb_list.p, p2_list.p, pa_counts);
   unsigned long long hc[2] = {0, 0};
+  uint64_t pa_tot = 0;
   GOD_CK(cudaMemcpyAsync(hc, pa_counts, sizeof(hc), cudaMemcpyDeviceToHost, st));
+  GOD_CK(cudaMemcpyAsync(&pa_tot, PA.seg_off.p + PA.n_seg, 8, cudaMemcpyDeviceToHost, st));
   GOD_CK(cudaStreamSynchronize(st));
+  GOD_TRY(scan_total_ok(pa_tot, "seed"));
   const uint64_t n_fb = hc[0], n_p2 = hc[1];
 
   // ---- fallback: full-length pattern alignment for reads with N in the prefix
@@ -717,9 +721,15 @@ int seed_device(const god_index* idx, const uint8_t* d_reads, const uint64_t* d_
   GOD_LAUNCH(classify_reads, grid_for(n), kT, 0, st, n, read_off.p, ltiny.p, lsmall.p, llarge.p, fill_counts);
   uint64_t total = 0;
   unsigned long long hf[3] = {0, 0, 0};
+  uint64_t set_tot[2] = {0, 0};
   GOD_CK(cudaMemcpyAsync(&total, read_off.p + n, 8, cudaMemcpyDeviceToHost, st));
   GOD_CK(cudaMemcpyAsync(hf, fill_counts, sizeof(hf), cudaMemcpyDeviceToHost, st));
+  if (n_fb) GOD_CK(cudaMemcpyAsync(&set_tot[0], FB.seg_off.p + FB.n_seg, 8, cudaMemcpyDeviceToHost, st));
+  if (n_p2) GOD_CK(cudaMemcpyAsync(&set_tot[1], P2.seg_off.p + P2.n_seg, 8, cudaMemcpyDeviceToHost, st));
   GOD_CK(cudaStreamSynchronize(st));
+  GOD_TRY(scan_total_ok(total, "seed"));
+  GOD_TRY(scan_total_ok(set_tot[0], "seed"));
+  GOD_TRY(scan_total_ok(set_tot[1], "seed"));
   *n_anchors = total;
   god_anchor* out = user_out;
   if (user_out) {

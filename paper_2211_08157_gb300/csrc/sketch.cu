@@ -1052,6 +1052,7 @@ int run_sketch_staged(const SketchJob& job, cudaStream_t st, StagedSketch& o, co
   uint64_t tot = 0;
   GOD_CK(cudaMemcpyAsync(&tot, o.sub_off.p + o.n_sub, 8, cudaMemcpyDeviceToHost, st));
   GOD_CK(cudaStreamSynchronize(st));
+  GOD_TRY(scan_total_ok(tot, "sketch"));
   o.total = tot;
   // algorithmic bytes: every patterned base read once, every record written once
   prof_add_work("sketch", (double)(job.V - job.n_seg) + 16.0 * (double)tot, (double)(job.V - job.n_seg));
