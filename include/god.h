@@ -227,15 +227,19 @@ int god_rmi_root_grad(const float *theta, int H, const float *x, const float *y,
 
 /* ----------------------------------------------------------------- memory
  * Releases an index, or an anchor array returned by god_seed / god_seed_device.
- * NULL is ignored. Device arrays are freed stream-ordered on the stream they
- * were allocated on. */
+ * NULL is ignored. Anchor arrays are freed stream-ordered on the stream they
+ * were allocated on; an index may be in use on any stream, so its release
+ * waits for the device once and then returns its arrays to the stream-ordered
+ * pool. */
 void god_free(void *p);
 
 /* Kernels launched by this library in this process so far. */
 uint64_t god_launch_count(void);
 
-/* Opt-in kernel timing: while enabled, every launch is bracketed by a pair of
- * CUDA events on its stream. god_prof_report writes a JSON object
+/* Opt-in kernel timing: while enabled (on = 1), every launch is bracketed by a
+ * pair of CUDA events on its stream; on = 2 times only the sketch kernel's
+ * launches (two events per launch, so the rest of a timed step runs as
+ * without timing); 0 switches timing off. god_prof_report writes a JSON object
  * {"kernel": [launches, total_ms, algorithmic_bytes, units], ...} (bytes and
  * units are filled in for the sketch kernel: patterned bases read plus 16-byte
  * minimizer records written; and for the lookups: 32 bytes per probe) of

@@ -262,16 +262,12 @@ static void free_index(god_index* idx) {
   int prev = 0;
   cudaGetDevice(&prev);
   cudaSetDevice(idx->device);
-  if (idx->d_arena) {
-    cudaFree(idx->d_arena);  // keys, offsets and leaves live in the arena
-  } else {
-    cudaFree(idx->d_keys);
-    cudaFree(idx->d_start);
-    cudaFree(idx->d_leaves);
-  }
-  cudaFree(idx->d_ent);
-  cudaFree(idx->d_ht);
-  cudaFree(idx->d_root);
+  // any stream may still use the index: wait for the device once, then hand
+  // the arrays back to the stream-ordered pool (no per-array synchronisation)
+  cudaDeviceSynchronize();
+  void* arrays[6] = {idx->d_keys, idx->d_start, idx->d_leaves, idx->d_ent, idx->d_ht, idx->d_root};
+  for (void* a : arrays)
+    if (a) cudaFreeAsync(a, 0);
   cudaSetDevice(prev);
   delete idx;
 }
@@ -303,7 +299,7 @@ void god_set_graphs(int on) { g_graphs_on.store(on ? 1 : 0); }
 
 void god_prof_enable(int on) {
   if (!on) prof_collect();
-  g_prof_on.store(on ? 1 : 0);
+  g_prof_on.store(on == 2 ? 2 : (on ? 1 : 0));
 }
 
 void god_prof_reset(void) {
@@ -319,6 +315,7 @@ int god_prof_report(char* buf, uint64_t cap) {
     std::lock_guard<std::mutex> lk(g_prof_mu);
     bool first = true;
     for (auto& kv : g_prof_tot) {
+      if (!kv.second.launches) continue;   // work recorded for a kernel that was not timed
       char item[320];
       snprintf(item, sizeof item, "%s\"%s\": [%llu, %.6f, %.1f, %.1f]", first ? "" : ", ", kv.first.c_str(),
                (unsigned long long)kv.second.launches, kv.second.ms, kv.second.bytes, kv.second.units);

@@ -30,6 +30,15 @@ int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
 extern std::atomic<uint64_t> g_launches;
 extern std::atomic<int> g_prof_on;
 // Opt-in per-kernel timing: an event pair around each launch, resolved later.
+// Mode 1 times every launch, mode 2 only the sketch kernel's.
+inline bool prof_wants(const char* kernel) {
+  const int m = g_prof_on.load(std::memory_order_relaxed);
+  if (m == 1) return true;
+  if (m != 2) return false;
+  const char* s = "sketch";
+  while (*s && *kernel == *s) ++s, ++kernel;
+  return *s == 0 && *kernel == 0;
+}
 void prof_begin(cudaStream_t st, cudaEvent_t* a);
 void prof_end(const char* name, cudaStream_t st, cudaEvent_t a);
 // Adds algorithmic bytes (and processed units) to a kernel's profile entry.
@@ -40,7 +49,7 @@ void prof_add_work(const char* name, double bytes, double units);
 #define GOD_LAUNCH(kernel, grid, block, smem, stream, ...)                       \
   do {                                                                           \
     cudaEvent_t _pa = nullptr;                                                   \
-    if (::god::g_prof_on.load(std::memory_order_relaxed)) ::god::prof_begin((stream), &_pa); \
+    if (::god::prof_wants(#kernel)) ::god::prof_begin((stream), &_pa);            \
     kernel<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);                  \
     ::god::g_launches.fetch_add(1, std::memory_order_relaxed);                   \
     cudaError_t _le = cudaGetLastError();                                        \
@@ -197,6 +206,8 @@ extern std::atomic<int> g_graphs_on;
 // Stable LSD radix sort of (key, value) pairs by bits [0, key_bits) of the key.
 // keys/vals are sorted in place (alternate buffers are allocated internally).
 int radix_sort_pairs(uint64_t* keys, uint64_t* vals, uint64_t n, int key_bits, cudaStream_t st);
+// The same with 32-bit values.
+int radix_sort_pairs32(uint64_t* keys, uint32_t* vals, uint64_t n, int key_bits, cudaStream_t st);
 
 // ------------------------------------------------------------------ index
 constexpr uint64_t kEmptyKey = ~0ULL;
@@ -216,7 +227,16 @@ struct RmiRoot {
   uint64_t kmin, kmax;
   float inv_span;
   uint32_t n_leaves;
+  // The trained 1 -> H -> 1 ReLU network as the piecewise-linear function it
+  // is: hinge points hx (ascending, +inf past the last) and, on piece i
+  // (hx[i - 1] <= x < hx[i]), f(x) = A[i] x + C[i]. Both the build's routing
+  // and every lookup evaluate this form (set by rmi_root_pieces).
+  float hx[kRootHidden];
+  float A[kRootHidden + 1];
+  float C[kRootHidden + 1];
 };
+// Fills R.hx, R.A, R.C from R.W1, R.b1, R.W2, R.b2 (host).
+void rmi_root_pieces(RmiRoot& R);
 
 struct DeviceIndex {           // what lookup kernels need, by value
   const uint64_t* keys;        // n_keys ascending
@@ -259,9 +279,6 @@ struct god_index {
   double rmi_mean_eps, rmi_fallback_key_frac;
   float rmi_loss;
   uint64_t device_bytes;
-  // learned index: keys, offsets and leaves in one allocation
-  void* d_arena;
-  size_t arena_bytes;
 };
 
 namespace god {

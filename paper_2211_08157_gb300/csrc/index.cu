@@ -26,9 +26,10 @@ inline unsigned blocks_for(uint64_t n, int per = kThreads) {
 
 // Staged sketch records of each warp sub-tile -> keys[] and vals[] =
 // (pos << 1) | z at their ordered place (warp per sub-tile).
+template <typename V>
 __global__ void split_staged(const MinRec* __restrict__ staging, const uint32_t* __restrict__ sub_cnt,
                              const uint64_t* __restrict__ sub_off, uint64_t n_sub, int WT, uint64_t* __restrict__ keys,
-                             uint64_t* __restrict__ vals) {
+                             V* __restrict__ vals) {
   const int lane = threadIdx.x & 31;
   const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x / 32);
   for (uint64_t sub = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) / 32; sub < n_sub; sub += warps) {
@@ -38,7 +39,7 @@ __global__ void split_staged(const MinRec* __restrict__ staging, const uint32_t*
     for (uint32_t i = lane; i < c; i += 32) {
       const uint4 r = __ldcs(reinterpret_cast<const uint4*>(src + i));   // read once
       keys[o + i] = ((uint64_t)r.y << 32) | r.x;
-      vals[o + i] = ((uint64_t)r.z << 1) | (r.w & 1u);
+      vals[o + i] = (V)(((uint64_t)r.z << 1) | (r.w & 1u));
     }
   }
 }
@@ -69,7 +70,8 @@ __global__ void run_heads(const uint64_t* __restrict__ keys, uint64_t n, uint32_
 }
 
 // Kept runs -> keys[U], start[U + 1], ent[E].
-__global__ void emit_runs(const uint64_t* __restrict__ keys, const uint64_t* __restrict__ vals, uint64_t n,
+template <typename V>
+__global__ void emit_runs(const uint64_t* __restrict__ keys, const V* __restrict__ vals, uint64_t n,
                           const uint64_t* __restrict__ rv, const uint64_t* __restrict__ roff,
                           uint64_t* __restrict__ out_keys, uint32_t* __restrict__ out_start,
                           uint64_t* __restrict__ out_ent) {
@@ -80,7 +82,7 @@ __global__ void emit_runs(const uint64_t* __restrict__ keys, const uint64_t* __r
       const uint32_t u = (uint32_t)(o >> 32), e = (uint32_t)o, len = (uint32_t)v;
       out_keys[u] = keys[i];
       out_start[u] = e;
-      for (uint32_t j = 0; j < len; ++j) out_ent[(uint64_t)e + j] = vals[i + j];
+      for (uint32_t j = 0; j < len; ++j) out_ent[(uint64_t)e + j] = (uint64_t)vals[i + j];
     }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -161,6 +163,52 @@ int lookup_keys(const DeviceIndex& di, const uint64_t* keys, size_t key_stride_b
   return GOD_OK;
 }
 
+// Sort the reference minimizers by key (values: (pos << 1) | z, 32-bit when
+// the reference is shorter than 2^31), cut runs, filter, and emit keys,
+// offsets and entries. U, E: kept keys and entries.
+template <typename V>
+int sort_and_emit(god_index* idx, StagedSketch& S, uint64_t n, cudaStream_t st, DBuf<uint64_t>& okeys,
+                  DBuf<uint32_t>& ostart, DBuf<uint64_t>& oent, uint64_t* U_out, uint64_t* E_out) {
+  DBuf<uint64_t> keys;
+  DBuf<V> vals;
+  GOD_TRY(keys.alloc(n, st));
+  GOD_TRY(vals.alloc(n, st));
+  const unsigned g = std::min<unsigned>(blocks_for(n), (unsigned)num_sms() * 32);
+  if (n) {
+    const uint64_t blocks = std::min<uint64_t>((S.n_sub * 32 + kThreads - 1) / kThreads, (uint64_t)num_sms() * 16);
+    GOD_LAUNCH(split_staged<V>, (unsigned)blocks, kThreads, 0, st, S.staging.p, S.sub_cnt.p, S.sub_off.p, S.n_sub,
+               S.WT, keys.p, vals.p);
+  }
+  S.staging.release();
+  if constexpr (sizeof(V) == 4)
+    GOD_TRY(radix_sort_pairs32(keys.p, vals.p, n, 2 * idx->k, st));
+  else
+    GOD_TRY(radix_sort_pairs(keys.p, vals.p, n, 2 * idx->k, st));
+
+  // runs of equal keys, the filter, and the output arrays
+  DBuf<uint64_t> rv, roff;
+  GOD_TRY(rv.alloc(n, st));
+  GOD_TRY(roff.alloc(n + 1, st));
+  if (n) GOD_LAUNCH(run_heads, g, kThreads, 0, st, keys.p, n, idx->max_occ, rv.p);
+  GOD_TRY(exclusive_scan_u64(rv.p, roff.p, n, st));
+  uint64_t tot = 0;
+  GOD_CK(cudaMemcpyAsync(&tot, roff.p + n, 8, cudaMemcpyDeviceToHost, st));
+  GOD_CK(cudaStreamSynchronize(st));
+  GOD_TRY(scan_total_ok(tot, "index"));
+  const uint64_t U = tot >> 32, E = tot & 0xFFFFFFFFULL;
+  GOD_TRY(okeys.alloc(U, st));
+  GOD_TRY(ostart.alloc(U + 1, st));
+  GOD_TRY(oent.alloc(E, st));
+  if (n) {
+    GOD_LAUNCH(emit_runs<V>, g, kThreads, 0, st, keys.p, vals.p, n, rv.p, roff.p, okeys.p, ostart.p, oent.p);
+  } else {
+    GOD_CK(cudaMemsetAsync(ostart.p, 0, sizeof(uint32_t), st));
+  }
+  *U_out = U;
+  *E_out = E;
+  return GOD_OK;
+}
+
 // ------------------------------------------------------------------ build
 int build_index_device(god_index* idx, const uint8_t* d_ref, uint64_t len, cudaStream_t st) {
   const PatternInfo& P = idx->pat;
@@ -190,39 +238,13 @@ int build_index_device(god_index* idx, const uint8_t* d_ref, uint64_t len, cudaS
   const uint64_t n = S.total;
   idx->n_min = n;
 
-  DBuf<uint64_t> keys, vals;
-  GOD_TRY(keys.alloc(n, st));
-  GOD_TRY(vals.alloc(n, st));
-  const unsigned g = std::min<unsigned>(blocks_for(n), (unsigned)num_sms() * 32);
-  if (n) {
-    const uint64_t blocks = std::min<uint64_t>((S.n_sub * 32 + kThreads - 1) / kThreads, (uint64_t)num_sms() * 16);
-    GOD_LAUNCH(split_staged, (unsigned)blocks, kThreads, 0, st, S.staging.p, S.sub_cnt.p, S.sub_off.p, S.n_sub, S.WT,
-               keys.p, vals.p);
-  }
-  S.staging.release();
-  GOD_TRY(radix_sort_pairs(keys.p, vals.p, n, 2 * idx->k, st));
-
-  // runs of equal keys, the filter, and the output arrays
-  DBuf<uint64_t> rv, roff;
-  GOD_TRY(rv.alloc(n, st));
-  GOD_TRY(roff.alloc(n + 1, st));
-  if (n) GOD_LAUNCH(run_heads, g, kThreads, 0, st, keys.p, n, idx->max_occ, rv.p);
-  GOD_TRY(exclusive_scan_u64(rv.p, roff.p, n, st));
-  uint64_t tot = 0;
-  GOD_CK(cudaMemcpyAsync(&tot, roff.p + n, 8, cudaMemcpyDeviceToHost, st));
-  GOD_CK(cudaStreamSynchronize(st));
-  GOD_TRY(scan_total_ok(tot, "index"));
-  const uint64_t U = tot >> 32, E = tot & 0xFFFFFFFFULL;
   DBuf<uint64_t> okeys, oent;
   DBuf<uint32_t> ostart;
-  GOD_TRY(okeys.alloc(U, st));
-  GOD_TRY(ostart.alloc(U + 1, st));
-  GOD_TRY(oent.alloc(E, st));
-  if (n) {
-    GOD_LAUNCH(emit_runs, g, kThreads, 0, st, keys.p, vals.p, n, rv.p, roff.p, okeys.p, ostart.p, oent.p);
-  } else {
-    GOD_CK(cudaMemsetAsync(ostart.p, 0, sizeof(uint32_t), st));
-  }
+  uint64_t U = 0, E = 0;
+  if (len < (1ULL << 31))
+    GOD_TRY(sort_and_emit<uint32_t>(idx, S, n, st, okeys, ostart, oent, &U, &E));
+  else
+    GOD_TRY(sort_and_emit<uint64_t>(idx, S, n, st, okeys, ostart, oent, &U, &E));
   // hash table at load <= 1/2; the slot word splits 64 bits into the quotient
   // (2k - lc bits), the rank (rb bits) and the displacement (the rest, >= 9
   // bits for k <= 28 since 2^lc >= 2U)

@@ -94,16 +94,17 @@ __global__ void __launch_bounds__(kRsScanThreads) rs_scan_rows(uint32_t* cnt, in
   if (threadIdx.x == 0) tot[blockIdx.x] = carry;
 }
 
+template <typename V>
 __global__ void __launch_bounds__(kRsThreads, 3) rs_scatter(const uint64_t* __restrict__ keys_in,
-                                                         const uint64_t* __restrict__ vals_in,
+                                                         const V* __restrict__ vals_in,
                                                          uint64_t* __restrict__ keys_out,
-                                                         uint64_t* __restrict__ vals_out, uint64_t n, int shift,
+                                                         V* __restrict__ vals_out, uint64_t n, int shift,
                                                          int bits, const uint32_t* __restrict__ offs,
                                                          const uint32_t* __restrict__ tot) {
   extern __shared__ __align__(16) unsigned char smem[];
   uint64_t* sk = reinterpret_cast<uint64_t*>(smem);          // kRsTile keys
-  uint64_t* sv = sk + kRsTile;                               // kRsTile values
-  uint32_t* whist = reinterpret_cast<uint32_t*>(sv + kRsTile);  // [warps][bins]
+  V* sv = reinterpret_cast<V*>(sk + kRsTile);                // kRsTile values
+  uint32_t* whist = reinterpret_cast<uint32_t*>(sk + 2 * kRsTile);  // [warps][bins] (room for 8-byte values)
   uint32_t* dstart = whist + kRsWarps * kRsMaxBins;           // [bins] tile-local digit start
   uint32_t* run = dstart + kRsMaxBins;                        // [bins] running output offset
   __shared__ uint32_t warp_tot[kRsWarps];
@@ -217,9 +218,8 @@ size_t scatter_smem() {
   return (size_t)kRsTile * 16 + (size_t)kRsWarps * kRsMaxBins * 4 + 2 * kRsMaxBins * 4;
 }
 
-}  // namespace
-
-int radix_sort_pairs(uint64_t* keys, uint64_t* vals, uint64_t n, int key_bits, cudaStream_t st) {
+template <typename V>
+int radix_sort_impl(uint64_t* keys, V* vals, uint64_t n, int key_bits, cudaStream_t st) {
   if (n <= 1 || key_bits <= 0) return GOD_OK;
   if (n >= (1ULL << 32)) {
     set_error("radix sort: at most 2^32 - 1 pairs");
@@ -230,33 +230,40 @@ int radix_sort_pairs(uint64_t* keys, uint64_t* vals, uint64_t n, int key_bits, c
   const int bits = (key_bits + passes - 1) / passes;
   const int bins = 1 << bits;
   const size_t smem = scatter_smem();
-  GOD_CK(cudaFuncSetAttribute(rs_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  GOD_CK(cudaFuncSetAttribute(rs_scatter<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
-  GOD_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rs_scatter, kRsThreads, smem));
+  GOD_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rs_scatter<V>, kRsThreads, smem));
   const uint64_t tiles = (n + kRsTile - 1) / kRsTile;
   const int G = (int)std::max<uint64_t>(1, std::min<uint64_t>(tiles, (uint64_t)num_sms() * std::max(per_sm, 1)));
   const uint64_t m = (uint64_t)bins * G;
-  if (m > (1u << 20)) {
-    set_error("radix sort: too many (digit, range) counts");
-    return GOD_EINVAL;
-  }
-  DBuf<uint64_t> k2, v2;
+  DBuf<uint64_t> k2;
+  DBuf<V> v2;
   DBuf<uint32_t> cnt, tot;
   GOD_TRY(k2.alloc(n, st));
   GOD_TRY(v2.alloc(n, st));
   GOD_TRY(cnt.alloc(m, st));
   GOD_TRY(tot.alloc(bins, st));
-  uint64_t *ki = keys, *vi = vals, *ko = k2.p, *vo = v2.p;
+  uint64_t *ki = keys, *ko = k2.p;
+  V *vi = vals, *vo = v2.p;
   for (int ps = 0; ps < passes; ++ps) {
     const int shift = ps * bits;
     GOD_LAUNCH(rs_count, (unsigned)G, kRsThreads, 0, st, ki, n, shift, bits, cnt.p);
     GOD_LAUNCH(rs_scan_rows, (unsigned)bins, kRsScanThreads, 0, st, cnt.p, G, tot.p);
-    GOD_LAUNCH(rs_scatter, (unsigned)G, kRsThreads, smem, st, ki, vi, ko, vo, n, shift, bits, cnt.p, tot.p);
+    GOD_LAUNCH(rs_scatter<V>, (unsigned)G, kRsThreads, smem, st, ki, vi, ko, vo, n, shift, bits, cnt.p, tot.p);
     std::swap(ki, ko);
     std::swap(vi, vo);
   }
   // passes is even: ki == keys
   return GOD_OK;
+}
+
+}  // namespace
+
+int radix_sort_pairs(uint64_t* keys, uint64_t* vals, uint64_t n, int key_bits, cudaStream_t st) {
+  return radix_sort_impl(keys, vals, n, key_bits, st);
+}
+int radix_sort_pairs32(uint64_t* keys, uint32_t* vals, uint64_t n, int key_bits, cudaStream_t st) {
+  return radix_sort_impl(keys, vals, n, key_bits, st);
 }
 
 }  // namespace god

@@ -309,6 +309,50 @@ __global__ void leaf_monotone(const uint64_t* leaf, uint64_t U, int* flag) {
     if (leaf[i] > leaf[i + 1]) *flag = 1;
 }
 
+}  // namespace
+
+// The network f(x) = b2 + sum_h W2[h] relu(W1[h] x + b1[h]) is linear between
+// consecutive hinge points -b1[h] / W1[h]; on each piece the active units are
+// those with W1[h] x + b1[h] > 0 at an interior point, A = sum of W2 W1 and
+// C = b2 + sum of W2 b1 over them (units with W1 = 0 add W2 relu(b1) to every
+// piece). Built in double, stored in FP32.
+void rmi_root_pieces(RmiRoot& R) {
+  double hs[kRootHidden];
+  int nh = 0;
+  for (int h = 0; h < kRootHidden; ++h) {
+    if (R.W1[h] == 0.0f) continue;
+    const double t = -(double)R.b1[h] / (double)R.W1[h];
+    if (std::isfinite(t)) hs[nh++] = t;
+  }
+  std::sort(hs, hs + nh);
+  for (int i = 0; i < kRootHidden; ++i) R.hx[i] = i < nh ? (float)hs[i] : INFINITY;
+  for (int i = 0; i <= kRootHidden; ++i) {
+    if (i > nh) {
+      R.A[i] = R.A[nh];
+      R.C[i] = R.C[nh];
+      continue;
+    }
+    double mid;
+    if (nh == 0) mid = 0.0;
+    else if (i == 0) mid = hs[0] - 1.0;
+    else if (i == nh) mid = hs[nh - 1] + 1.0;
+    else mid = 0.5 * (hs[i - 1] + hs[i]);
+    double A = 0.0, C = R.b2;
+    for (int h = 0; h < kRootHidden; ++h) {
+      if (R.W1[h] == 0.0f) {
+        C += (double)R.W2[h] * std::max(0.0, (double)R.b1[h]);
+      } else if ((double)R.W1[h] * mid + (double)R.b1[h] > 0.0) {
+        A += (double)R.W2[h] * R.W1[h];
+        C += (double)R.W2[h] * R.b1[h];
+      }
+    }
+    R.A[i] = (float)A;
+    R.C[i] = (float)C;
+  }
+}
+
+namespace {
+
 void init_root(RmiRoot* R, int kind) {
   // Knots of a piecewise-linear basis on [0, 1]: hidden unit h = relu(x - h/H);
   // output weights drawn from a fixed-seed generator (splitmix64). The linear
@@ -440,6 +484,7 @@ int build_rmi(god_index* idx, cudaStream_t st) {
     for (int h = 0; h < H; ++h) { R.W1[h] = th[h]; R.b1[h] = th[H + h]; R.W2[h] = th[2 * H + h]; }
     R.b2 = th[3 * H];
   }
+  rmi_root_pieces(R);
   GOD_CK(cudaMemcpyAsync(d_root.p, &R, sizeof(R), cudaMemcpyHostToDevice, st));
 
   // route every key, group by leaf (stable: ranks stay ascending), fit leaves
@@ -478,26 +523,7 @@ int build_rmi(god_index* idx, cudaStream_t st) {
   GOD_CK(cudaStreamSynchronize(st));
   idx->root = R;
   idx->d_root = d_root.take();
-  // one arena [keys | offsets | leaves]: the structure a learned lookup touches
-  {
-    const size_t kb = ((U * 8) + 255) & ~(size_t)255;
-    const size_t sb = (((U + 1) * 4) + 255) & ~(size_t)255;
-    const size_t lb = (size_t)n_leaves * sizeof(RmiLeaf);
-    void* arena = nullptr;
-    GOD_TRY(dmalloc(&arena, kb + sb + lb, st));
-    char* a8 = static_cast<char*>(arena);
-    GOD_CK(cudaMemcpyAsync(a8, idx->d_keys, U * 8, cudaMemcpyDeviceToDevice, st));
-    GOD_CK(cudaMemcpyAsync(a8 + kb, idx->d_start, (U + 1) * 4, cudaMemcpyDeviceToDevice, st));
-    GOD_CK(cudaMemcpyAsync(a8 + kb + sb, leaves.p, lb, cudaMemcpyDeviceToDevice, st));
-    GOD_CK(cudaStreamSynchronize(st));
-    dfree(idx->d_keys, st);
-    dfree(idx->d_start, st);
-    idx->d_keys = reinterpret_cast<uint64_t*>(a8);
-    idx->d_start = reinterpret_cast<uint32_t*>(a8 + kb);
-    idx->d_leaves = reinterpret_cast<RmiLeaf*>(a8 + kb + sb);
-    idx->d_arena = arena;
-    idx->arena_bytes = kb + sb + lb;
-  }
+  idx->d_leaves = leaves.take();
   idx->has_rmi = 1;
   idx->rmi_mean_eps = (double)hs[0] / (double)U;
   idx->rmi_fallback_leaves = (uint32_t)hs[3];

@@ -8,15 +8,16 @@
 
 namespace god {
 
+// Root model at the key: the piece holding x (bisection over the hinge
+// points) and one multiply-add.
 __device__ __forceinline__ float rmi_root_eval(const RmiRoot& R, uint64_t key) {
   const float x = __fmul_rn(__ull2float_rn(key - R.kmin), R.inv_span);
-  float f = R.b2;
+  int i = 0;
 #pragma unroll
-  for (int h = 0; h < kRootHidden; ++h) {
-    const float a = fmaxf(__fmaf_rn(R.W1[h], x, R.b1[h]), 0.0f);
-    f = __fmaf_rn(R.W2[h], a, f);
-  }
-  return f;
+  for (int step = kRootHidden / 2; step > 0; step >>= 1)
+    if (R.hx[i + step - 1] <= x) i += step;
+  if (R.hx[i] <= x) ++i;   // i = hinges <= x (0..32)
+  return __fmaf_rn(R.A[i], x, R.C[i]);
 }
 
 __device__ __forceinline__ uint32_t rmi_root_leaf(const RmiRoot& R, uint64_t key) {
@@ -83,25 +84,28 @@ __device__ __forceinline__ bool rmi_in_range(const RmiRoot& R, uint64_t key) {
   return key >= R.kmin && key <= R.kmax;
 }
 
-// Rank of key in keys[] inside the leaf's window, kNoRank when absent. A
-// window of at most 8 keys is read at once (independent loads) and scanned;
-// wider windows are bisected.
+// Rank of key in keys[] inside the leaf's window [pred - eps, pred + eps],
+// kNoRank when absent. A window of at most 8 keys is read at once
+// (independent loads) and scanned; wider ones are bisected.
+template <int N>
+__device__ __forceinline__ uint64_t key_scan(const DeviceIndex& di, int64_t lo, int64_t hi, uint64_t key) {
+  uint64_t km[N];
+#pragma unroll
+  for (int t = 0; t < N; ++t) km[t] = lo + t <= hi ? __ldg(di.keys + lo + t) : ~0ULL;
+  uint64_t r = kNoRank;
+#pragma unroll
+  for (int t = 0; t < N; ++t)
+    if (lo + t <= hi && km[t] == key) r = (uint64_t)(lo + t);
+  return r;
+}
+
 __device__ __forceinline__ uint64_t rmi_rank_in_leaf(const DeviceIndex& di, const RmiLeaf& L, uint64_t key) {
   const uint32_t eps = (uint32_t)(L.base_eps >> 56);
   const int64_t pred = rmi_leaf_pred(L.slope, L.icept, L.base_eps & ((1ULL << 56) - 1), key);
   int64_t lo = pred - (int64_t)eps, hi = pred + (int64_t)eps;
   if (lo < 0) lo = 0;
   if (hi > (int64_t)di.n_keys - 1) hi = (int64_t)di.n_keys - 1;
-  if (hi - lo < 8) {
-    uint64_t km[8];
-#pragma unroll
-    for (int t = 0; t < 8; ++t) km[t] = lo + t <= hi ? __ldg(di.keys + lo + t) : ~0ULL;
-    uint64_t r = kNoRank;
-#pragma unroll
-    for (int t = 0; t < 8; ++t)
-      if (lo + t <= hi && km[t] == key) r = (uint64_t)(lo + t);
-    return r;
-  }
+  if (hi - lo < 8) return key_scan<8>(di, lo, hi, key);   // one width: lanes of a warp stay together
   while (lo <= hi) {
     const int64_t mid = (lo + hi) >> 1;
     const uint64_t km = __ldg(di.keys + mid);

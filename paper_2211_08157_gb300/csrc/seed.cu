@@ -518,6 +518,7 @@ __global__ void __launch_bounds__(kT) compact_lookup(const MinRec* __restrict__ 
         key[u] = ((uint64_t)r.y << 32) | r.x;
         pzv[u] = (r.z << 1) | (r.w & 1u);
       }
+      uint64_t pay[U];
       if (VIA == 1) {
         RmiLeaf L[U];
         bool hashed[U];
@@ -529,8 +530,7 @@ __global__ void __launch_bounds__(kT) compact_lookup(const MinRec* __restrict__ 
 #pragma unroll
         for (int u = 0; u < U; ++u) {
           hashed[u] = hashed[u] || (uint32_t)(L[u].base_eps >> 56) > di.eps_max;
-          rk[u] = !ok[u] ? kNoRank : hashed[u] ? ht_rank(di, key[u], ht_home_word(di, key[u]))
-                                                 : rmi_rank_in_leaf(di, L[u], key[u]);
+          pay[u] = !ok[u] ? 0 : hashed[u] ? ht_find(di, key[u]) : rank_payload(di, rmi_rank_in_leaf(di, L[u], key[u]));
         }
       } else {
         uint64_t w[U];
@@ -538,12 +538,14 @@ __global__ void __launch_bounds__(kT) compact_lookup(const MinRec* __restrict__ 
         for (int u = 0; u < U; ++u) w[u] = ok[u] ? ht_home_word(di, key[u]) : kEmptyKey;
 #pragma unroll
         for (int u = 0; u < U; ++u) rk[u] = ok[u] ? ht_rank(di, key[u], w[u]) : kNoRank;
+#pragma unroll
+        for (int u = 0; u < U; ++u) pay[u] = rank_payload(di, rk[u]);
       }
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         if (ok[u]) {
           pz[o + i0 + 32 * u] = pzv[u];
-          sc[o + i0 + 32 * u] = rank_payload(di, rk[u]);
+          sc[o + i0 + 32 * u] = pay[u];
         }
       }
     }
