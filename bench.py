@@ -238,25 +238,42 @@ def run_reference(args, ws, rank):
 
 
 # ----------------------------------------------------------------------------- serving
-def serving_pool(ref, seed=5):
+def serving_pool(ref, long_max=300, seed=5):
     """Request payloads: short-read batches (1k-50k x 150 bp) and long-read batches
-    (HiFi-like and ONT-like; 10-300 reads here, the 2,000-read upper end is capped
-    to keep generation fast), each kind a third of the stream."""
+    (HiFi-like and ONT-like, 10-long_max reads), each kind a third of the stream."""
     rng = np.random.default_rng(seed)
     pool = {"short": [], "hifi": [], "ont": []}
     for i in range(8):
         g = np.random.default_rng(seed * 100 + i)
         pool["short"].append(synth.reads(ref, int(rng.integers(1000, 50001)), synth.SHORT, synth.ILLUMINA_INDEL, 0,
                                          rng=g)[:2])
-        pool["hifi"].append(synth.reads(ref, int(rng.integers(10, 301)), synth.HIFI, synth.HIFI_ERR, 0, rng=g)[:2])
-        ont = synth.LengthModel("lognormal", mu=synth.ONT.mu, sigma=synth.ONT.sigma, lo=500, hi=30_000)
-        pool["ont"].append(synth.reads(ref, int(rng.integers(10, 301)), ont, synth.ONT_ERR, 0, rng=g)[:2])
+        pool["hifi"].append(synth.reads(ref, int(rng.integers(10, long_max + 1)), synth.HIFI, synth.HIFI_ERR, 0,
+                                        rng=g)[:2])
+        pool["ont"].append(synth.reads(ref, int(rng.integers(10, long_max + 1)), synth.ONT, synth.ONT_ERR, 0,
+                                       rng=g)[:2])
     return pool
 
 
-def run_serving(god, idx, pool, rate, duration, mode, slots=4, seed=11):
+def seed_host(god, idx, reads, offs, via):
+    """god_seed_into with host buffers and an explicit lookup path (grows the
+    output on GOD_ERANGE)."""
+    cap = max(1024, int(offs[-1]) // 8)
+    while True:
+        out = np.empty((cap, 4), np.uint32)
+        try:
+            m = god.god_seed_into(idx, reads, offs, out, via=via)
+            return out[:m]
+        except god.GodError as e:
+            if e.rc != -5:
+                raise
+            cap = max(cap * 2, int(getattr(e, "needed", 0) or 0))
+
+
+def run_serving(god, idx, pool, rate, duration, mode, slots=4, seed=11, saturate=False, via=None):
     """Poisson arrivals at `rate`/s for `duration` s. mode 'server': the
-    continuous-batching server; 'plain': one god_seed call per request, FIFO."""
+    continuous-batching server; 'plain': one god_seed call per request, FIFO
+    (index path `via`). saturate: every request arrives at time 0 (the
+    throughput the path sustains; latency then includes the queue)."""
     import queue
     rng = np.random.default_rng(seed)
     kinds = ["short", "hifi", "ont"]
@@ -264,7 +281,7 @@ def run_serving(god, idx, pool, rate, duration, mode, slots=4, seed=11):
     while t < duration:
         t += rng.exponential(1.0 / rate)
         kind = kinds[int(rng.integers(0, 3))]
-        arrivals.append((t, pool[kind][int(rng.integers(0, len(pool[kind])))]))
+        arrivals.append((0.0 if saturate else t, pool[kind][int(rng.integers(0, len(pool[kind])))]))
     lat, bases = [], 0
     t0 = time.perf_counter()
     if mode == "server":
@@ -298,7 +315,10 @@ def run_serving(god, idx, pool, rate, duration, mode, slots=4, seed=11):
             now = time.perf_counter() - t0
             if at > now:
                 time.sleep(at - now)
-            god.god_seed(idx, r, o)
+            if via is None:
+                god.god_seed(idx, r, o)
+            else:
+                seed_host(god, idx, r, o, via)
             lat.append(time.perf_counter() - t0 - at)
             bases += int(o[-1])
     wall = time.perf_counter() - t0
@@ -325,6 +345,9 @@ def main():
     ap.add_argument("--no-compare", action="store_true", help="skip the other index kind's seed-only line")
     ap.add_argument("--serving-seconds", type=float, default=3.0, help="0 skips the serving measurement")
     ap.add_argument("--serving-rate", type=float, default=200.0)
+    ap.add_argument("--serving-workload", default="ont_3100mbp_100k",
+                    help="reference of the served index (the 3.1 Gbp one by default)")
+    ap.add_argument("--serving-long-max", type=int, default=2000, help="largest long-read request (reads)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gb300":
         args.warmup = 3
@@ -507,20 +530,37 @@ def main():
                "h2d_bytes_per_step": int(ref.nbytes + reads.nbytes + offs.nbytes),
                "d2h_bytes_per_step": int(m * 16), "ms_per_step": e2e_s * 1e3}
 
-    # ---- serving: Poisson request stream against the resident index
+    # ---- serving: request streams against a resident index; the server (the
+    # index's learned lookups, continuous batching) against the plain path (one
+    # god_seed call per request, hash lookups)
     serving = None
     if args.serving_seconds > 0 and rank == 0:
-        pool = serving_pool(ref)
-        sp = god.god_params_init(index_kind=kind, pa_t=wl.t)
-        sidx = god.god_build_index(d_ref, wl.pattern, wl.k, wl.w, wl.max_occ, params=sp)
+        swl = synth.WORKLOADS[args.serving_workload]
+        sref = ref if swl.name == wl.name else swl.make_reference()
+        pool = serving_pool(sref, long_max=args.serving_long_max)
+        sp = god.god_params_init(index_kind=god.GOD_INDEX_LEARNED, pa_t=swl.t)
+        t0 = time.perf_counter()
+        sidx = god.god_build_index(sref, swl.pattern, swl.k, swl.w, swl.max_occ, params=sp)
+        build_s = time.perf_counter() - t0
         run_serving(god, sidx, pool, args.serving_rate, 0.5, "server")   # warm-up
-        serving = {"index": args.index, "rate_per_s": args.serving_rate, "seconds": args.serving_seconds,
-                   "mix": "1/3 short (1k-50k x 150 bp), 1/3 HiFi-like, 1/3 ONT-like (10-300 reads), "
-                          "on the benchmark's 100 Mbp index",
-                   "continuous_batching": run_serving(god, sidx, pool, args.serving_rate, args.serving_seconds,
-                                                      "server"),
-                   "plain_one_at_a_time": run_serving(god, sidx, pool, args.serving_rate, args.serving_seconds,
-                                                      "plain")}
+        n_sat = max(1, int(args.serving_rate * args.serving_seconds))
+        serving = {"workload": swl.name, "ref_bases": int(sref.size), "index": "learned (server) / hash (plain)",
+                   "index_build_s_from_host": build_s, "index_info": {k: sidx.info[k] for k in
+                                                                      ("n_keys", "n_entries", "rmi_mean_eps")},
+                   "mix": f"1/3 short (1k-50k x 150 bp), 1/3 HiFi-like, 1/3 ONT-like (10-{args.serving_long_max} "
+                          f"reads) per request",
+                   "poisson": {"rate_per_s": args.serving_rate, "seconds": args.serving_seconds,
+                               "continuous_batching": run_serving(god, sidx, pool, args.serving_rate,
+                                                                  args.serving_seconds, "server"),
+                               "plain_hash_one_at_a_time": run_serving(god, sidx, pool, args.serving_rate,
+                                                                       args.serving_seconds, "plain", via=0)},
+                   "saturated": {"requests": n_sat, "note": "every request submitted at time 0",
+                                 "continuous_batching": run_serving(god, sidx, pool, args.serving_rate,
+                                                                    args.serving_seconds, "server",
+                                                                    saturate=True),
+                                 "plain_hash_one_at_a_time": run_serving(god, sidx, pool, args.serving_rate,
+                                                                         args.serving_seconds, "plain",
+                                                                         saturate=True, via=0)}}
         sidx.close()
 
     # ---- CPU oracle baseline (rank 0, N = 1 only)
