@@ -17,8 +17,8 @@
 //    per index entry; anchors are counted per read, offsets scanned, and each
 //    read's anchors are produced and sorted in on-chip memory in one step
 //    (a thread per read for lists of at most 16, a warp per read for short
-//    lists, a CTA per read with chunked bitonic sorts and merge-path passes for
-//    long ones).
+//    lists, a CTA per read with a shared-memory radix sort for long ones; lists
+//    past 4096 anchors are sorted in chunks merged by merge-path passes).
 #include <algorithm>
 #include <vector>
 
@@ -31,8 +31,9 @@ namespace {
 constexpr int kT = 256;
 constexpr uint32_t kSrcPA = 0, kSrcFB = 1, kSrcP2 = 2;
 constexpr int kSmallCap = 128;          // anchors per read for the warp path
-constexpr int kLargeThreads = 512;
-constexpr int kLargeCap = 8192;         // anchors sorted in shared memory at once
+constexpr int kLargeThreads = 256;
+constexpr int kLargeCap = 4096;         // anchors sorted in shared memory at once
+constexpr int kLargeRounds = kLargeCap / kLargeThreads;
 
 inline unsigned grid_for(uint64_t n, int per = kT, unsigned cap_mult = 32) {
   uint64_t b = (n + per - 1) / per;
@@ -206,12 +207,13 @@ __global__ void count_anchors_list(const uint32_t* __restrict__ list, uint32_t n
 // (CTA path). Lists are unordered; every read writes its own output range.
 __global__ void classify_reads(uint32_t n, const uint64_t* __restrict__ read_off, uint32_t* __restrict__ tiny,
                                uint32_t* __restrict__ small, uint32_t* __restrict__ large,
-                               unsigned long long* __restrict__ counts) {
+                               uint32_t* __restrict__ huge, unsigned long long* __restrict__ counts) {
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t c = read_off[i + 1] - read_off[i];
     warp_append(c > 0 && c <= kTinyCap, (uint32_t)i, tiny, counts + 0);
     warp_append(c > kTinyCap && c <= kSmallCap, (uint32_t)i, small, counts + 1);
-    warp_append(c > kSmallCap, (uint32_t)i, large, counts + 2);
+    warp_append(c > kSmallCap && c <= kLargeCap, (uint32_t)i, large, counts + 2);
+    warp_append(c > kLargeCap, (uint32_t)i, huge, counts + 3);
   }
 }
 
@@ -390,6 +392,10 @@ __device__ void fill_range(const RecSet& S, uint64_t beg, uint32_t cnt, const ui
   }
 }
 
+__device__ void key_field_bits(const uint64_t* s, uint32_t n, int* lo_bits, int* hi_bits, uint32_t* warp_buf);
+__device__ uint64_t* cta_radix_sort(uint64_t* a, uint64_t* b, uint32_t n, int lo_bits, int hi_bits,
+                                    uint32_t* whist, uint32_t* dstart, uint32_t* warp_buf);
+
 __device__ void bitonic_sort_smem(uint64_t* s, uint32_t n_pad) {
   for (uint32_t k = 2; k <= n_pad; k <<= 1) {
     for (uint32_t j = k >> 1; j > 0; j >>= 1) {
@@ -404,6 +410,123 @@ __device__ void bitonic_sort_smem(uint64_t* s, uint32_t n_pad) {
       __syncthreads();
     }
   }
+}
+
+// Sorted keys of s[0, n) (n <= kLargeCap): a bitonic network for up to 1024
+// keys (padded to a power of two with ~0), the radix sort past that. Returns
+// the buffer holding the result (s or t).
+__device__ uint64_t* cta_sort_keys(uint64_t* s, uint64_t* t, uint32_t n, uint32_t* whist, uint32_t* dstart,
+                                   uint32_t* warp_buf) {
+  if (n <= 1024) {
+    uint32_t n_pad = 1;
+    while (n_pad < n) n_pad <<= 1;
+    for (uint32_t q = n + threadIdx.x; q < n_pad; q += blockDim.x) s[q] = ~0ULL;
+    __syncthreads();
+    bitonic_sort_smem(s, n_pad);
+    return s;
+  }
+  int lb, hb;
+  key_field_bits(s, n, &lb, &hb, warp_buf);
+  return cta_radix_sort(s, t, n, lb, hb, whist, dstart, warp_buf);
+}
+
+// Stable CTA radix sort of a[0, n) (n <= kLargeCap) by the digits of bits
+// [0, lo_bits) and [32, 32 + hi_bits), 8 bits at a time (the anchor key's
+// read-position field and its reference-position field; bits outside them are
+// zero in every key). Warp w ranks the contiguous block of elements
+// [w C, w C + C) round by round: the lanes with an equal digit come from
+// ballots over the digit's bits, their count from a per-warp counter. Returns
+// the buffer (a or b) that holds the result.
+__device__ uint64_t* cta_radix_sort(uint64_t* a, uint64_t* b, uint32_t n, int lo_bits, int hi_bits,
+                                    uint32_t* whist, uint32_t* dstart, uint32_t* warp_buf) {
+  constexpr int W = kLargeThreads / 32;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  const uint32_t C = ((n + W * 32 - 1) / (W * 32)) * 32;   // elements per warp, a multiple of 32
+  const uint32_t w0 = wid * C, w1 = min(n, w0 + C);
+  for (int range = 0; range < 2; ++range) {
+    const int base = range ? 32 : 0, bits = range ? hi_bits : lo_bits;
+    for (int sh = 0; sh < bits; sh += 8) {
+      const int nb = min(8, bits - sh), shift = base + sh;
+      const uint32_t dmask = (1u << nb) - 1u;
+      for (int i = threadIdx.x; i < W * 256; i += kLargeThreads) whist[i] = 0;
+      __syncthreads();
+      uint32_t rank[kLargeRounds];
+      uint32_t* wh = whist + wid * 256;
+      const int rounds = (int)(C / 32);   // the same for every warp
+#pragma unroll
+      for (int r = 0; r < kLargeRounds; ++r) {
+        if (r >= rounds) break;
+        const uint32_t idx = w0 + r * 32 + lane;
+        const bool ok = idx < w1;
+        const uint32_t d = ok ? (uint32_t)(a[idx] >> shift) & dmask : 0u;
+        unsigned peers = __ballot_sync(0xffffffffu, ok);
+        for (int t = 0; t < nb; ++t) {
+          const bool one = (d >> t) & 1u;
+          const unsigned bal = __ballot_sync(0xffffffffu, one);
+          peers &= one ? bal : ~bal;
+        }
+        const uint32_t before = ok ? wh[d] : 0u;
+        __syncwarp();
+        if (ok && (peers & lt) == 0) wh[d] = before + __popc(peers);
+        __syncwarp();
+        rank[r] = before + __popc(peers & lt);
+      }
+      __syncthreads();
+      uint32_t cnt = 0;
+      if (threadIdx.x < 256) {
+        for (int w = 0; w < W; ++w) {
+          const uint32_t x = whist[w * 256 + threadIdx.x];
+          whist[w * 256 + threadIdx.x] = cnt;
+          cnt += x;
+        }
+      }
+      uint32_t tot;
+      const uint32_t ds = block_excl_scan_u32(cnt, &tot, warp_buf);
+      if (threadIdx.x < 256) dstart[threadIdx.x] = ds;
+      __syncthreads();
+#pragma unroll
+      for (int r = 0; r < kLargeRounds; ++r) {
+        if (r >= rounds) break;
+        const uint32_t idx = w0 + r * 32 + lane;
+        if (idx < w1) {
+          const uint64_t key = a[idx];
+          const uint32_t d = (uint32_t)(key >> shift) & dmask;
+          b[dstart[d] + whist[wid * 256 + d] + rank[r]] = key;
+        }
+      }
+      __syncthreads();
+      uint64_t* t = a;
+      a = b;
+      b = t;
+    }
+  }
+  return a;
+}
+
+// Bits needed by the read-position field (bits 0..31) and the reference
+// position field (bits 32..63) of the keys s[0, n) (block-wide maxima).
+__device__ void key_field_bits(const uint64_t* s, uint32_t n, int* lo_bits, int* hi_bits, uint32_t* warp_buf) {
+  if (threadIdx.x == 0) {
+    warp_buf[0] = 0;
+    warp_buf[1] = 0;
+  }
+  __syncthreads();
+  uint32_t lo = 0, hi = 0;
+  for (uint32_t q = threadIdx.x; q < n; q += blockDim.x) {
+    lo |= (uint32_t)s[q];
+    hi |= (uint32_t)(s[q] >> 32);
+  }
+  lo = __reduce_or_sync(0xffffffffu, lo);
+  hi = __reduce_or_sync(0xffffffffu, hi);
+  if ((threadIdx.x & 31) == 0) {
+    atomicOr(&warp_buf[0], lo);
+    atomicOr(&warp_buf[1], hi);
+  }
+  __syncthreads();
+  *lo_bits = 32 - __clz(warp_buf[0]);
+  *hi_bits = 32 - __clz(warp_buf[1]);
+  __syncthreads();
 }
 
 // CTA merge of sorted a[0, na) and b[0, nb) into o (merge path per thread).
@@ -424,16 +547,30 @@ __device__ void cta_merge(const uint64_t* a, uint64_t na, const uint64_t* b, uin
   }
 }
 
+// CTAs take reads from a shared counter, the lists past kLargeCap anchors
+// (chunked, the longest work) first.
 __global__ void __launch_bounds__(kLargeThreads) fill_sort_large(RecSets sets, const uint32_t* __restrict__ src,
                                                                  const uint32_t* __restrict__ seed_seg,
                                                                  const uint64_t* __restrict__ read_off,
-                                                                 const uint32_t* __restrict__ list, uint32_t nl,
+                                                                 const uint32_t* __restrict__ huge, uint32_t n_huge,
+                                                                 const uint32_t* __restrict__ large, uint32_t n_large,
                                                                  const uint64_t* __restrict__ ent,
-                                                                 god_anchor* __restrict__ out, uint64_t* tmp) {
-  extern __shared__ __align__(16) uint64_t sk[];  // kLargeCap keys
+                                                                 god_anchor* __restrict__ out, uint64_t* tmp,
+                                                                 unsigned int* queue) {
+  extern __shared__ __align__(16) uint64_t sk[];  // two buffers of kLargeCap keys, then radix counters
+  uint64_t* sb = sk + kLargeCap;
+  uint32_t* whist = reinterpret_cast<uint32_t*>(sb + kLargeCap);
+  uint32_t* dstart = whist + (kLargeThreads / 32) * 256;
   __shared__ uint32_t warp_buf[kLargeThreads / 32 + 1];
-  for (uint32_t li = blockIdx.x; li < nl; li += gridDim.x) {
-    const uint32_t i = list[li];
+  __shared__ uint32_t s_li;
+  const uint32_t nl = n_huge + n_large;
+  while (true) {
+    if (threadIdx.x == 0) s_li = atomicAdd(queue, 1u);
+    __syncthreads();
+    const uint32_t li = s_li;
+    __syncthreads();
+    if (li >= nl) break;
+    const uint32_t i = li < n_huge ? huge[li] : large[li - n_huge];
     const uint64_t off = read_off[i];
     const uint64_t n = read_off[i + 1] - off;
     const RecSet S = pick_set(sets, src[i]);
@@ -441,13 +578,10 @@ __global__ void __launch_bounds__(kLargeThreads) fill_sort_large(RecSets sets, c
     const uint64_t beg = S.seg_off[g];
     const uint32_t cnt = S.seg_cnt[g];
     if (n <= kLargeCap) {
-      uint32_t n_pad = 1;
-      while (n_pad < n) n_pad <<= 1;
       fill_range(S, beg, cnt, ent, 0, n, sk, warp_buf);
-      for (uint32_t q = (uint32_t)n + threadIdx.x; q < n_pad; q += blockDim.x) sk[q] = ~0ULL;
       __syncthreads();
-      bitonic_sort_smem(sk, n_pad);
-      for (uint32_t q = threadIdx.x; q < n; q += blockDim.x) store_anchor(out + off + q, i, sk[q]);
+      const uint64_t* srt = cta_sort_keys(sk, sb, (uint32_t)n, whist, dstart, warp_buf);
+      for (uint32_t q = threadIdx.x; q < n; q += blockDim.x) store_anchor(out + off + q, i, srt[q]);
       __syncthreads();
       continue;
     }
@@ -457,13 +591,10 @@ __global__ void __launch_bounds__(kLargeThreads) fill_sort_large(RecSets sets, c
     for (uint64_t c0 = 0; c0 < n; c0 += kLargeCap) {
       const uint64_t c1 = std::min<uint64_t>(n, c0 + kLargeCap);
       const uint32_t m = (uint32_t)(c1 - c0);
-      uint32_t n_pad = 1;
-      while (n_pad < m) n_pad <<= 1;
       fill_range(S, beg, cnt, ent, c0, c1, sk, warp_buf);
-      for (uint32_t q = m + threadIdx.x; q < n_pad; q += blockDim.x) sk[q] = ~0ULL;
       __syncthreads();
-      bitonic_sort_smem(sk, n_pad);
-      for (uint32_t q = threadIdx.x; q < m; q += blockDim.x) t0[c0 + q] = sk[q];
+      const uint64_t* srt = cta_sort_keys(sk, sb, m, whist, dstart, warp_buf);
+      for (uint32_t q = threadIdx.x; q < m; q += blockDim.x) t0[c0 + q] = srt[q];
       __syncthreads();
     }
     uint64_t* a = t0;
@@ -651,7 +782,8 @@ int seed_device(const god_index* idx, const uint8_t* d_reads, const uint64_t* d_
   GOD_CK(cudaMemsetAsync(ctl.p, 0, 8 * sizeof(unsigned long long), st));
   int* err = reinterpret_cast<int*>(ctl.p);
   unsigned long long* pa_counts = ctl.p + 1;     // [fallback, seeding pass]
-  unsigned long long* fill_counts = ctl.p + 3;   // [tiny, small, large]
+  unsigned long long* fill_counts = ctl.p + 3;   // [tiny, small, large, huge]
+  unsigned int* fill_queue = reinterpret_cast<unsigned int*>(ctl.p + 7);
   DBuf<uint32_t> need_full, shift, src, seed_seg, fb_list, p2_list;
   DBuf<uint64_t> read_cnt, read_off;
   GOD_TRY(need_full.alloc(n, st));
@@ -716,13 +848,15 @@ int seed_device(const god_index* idx, const uint8_t* d_reads, const uint64_t* d_
   sets.s[kSrcFB] = FB.view();
   sets.s[kSrcP2] = P2.view();
   GOD_TRY(exclusive_scan_u64(read_cnt.p, read_off.p, n, st));
-  DBuf<uint32_t> ltiny, lsmall, llarge;
+  DBuf<uint32_t> ltiny, lsmall, llarge, lhuge;
   GOD_TRY(ltiny.alloc(n, st));
   GOD_TRY(lsmall.alloc(n, st));
   GOD_TRY(llarge.alloc(n, st));
-  GOD_LAUNCH(classify_reads, grid_for(n), kT, 0, st, n, read_off.p, ltiny.p, lsmall.p, llarge.p, fill_counts);
+  GOD_TRY(lhuge.alloc(n, st));
+  GOD_LAUNCH(classify_reads, grid_for(n), kT, 0, st, n, read_off.p, ltiny.p, lsmall.p, llarge.p, lhuge.p,
+             fill_counts);
   uint64_t total = 0;
-  unsigned long long hf[3] = {0, 0, 0};
+  unsigned long long hf[4] = {0, 0, 0, 0};
   uint64_t set_tot[2] = {0, 0};
   GOD_CK(cudaMemcpyAsync(&total, read_off.p + n, 8, cudaMemcpyDeviceToHost, st));
   GOD_CK(cudaMemcpyAsync(hf, fill_counts, sizeof(hf), cudaMemcpyDeviceToHost, st));
@@ -743,21 +877,21 @@ int seed_device(const god_index* idx, const uint8_t* d_reads, const uint64_t* d_
   if (total == 0) return GOD_OK;
 
   // ---- fill + sort per read
-  const uint64_t n_tiny = hf[0], n_small = hf[1], n_large = hf[2];
+  const uint64_t n_tiny = hf[0], n_small = hf[1], n_large = hf[2], n_huge = hf[3];
   if (n_tiny)
     GOD_LAUNCH(fill_sort_tiny, grid_for(n_tiny, kT, 64), kT, 0, st, sets, src.p, seed_seg.p, read_off.p, ltiny.p,
                (uint32_t)n_tiny, idx->d_ent, out);
   if (n_small)
     GOD_LAUNCH(fill_sort_small, grid_for(n_small * 32, kT, 64), kT, 0, st, sets, src.p, seed_seg.p, read_off.p,
                lsmall.p, (uint32_t)n_small, idx->d_ent, out);
-  if (n_large) {
+  if (n_large + n_huge) {
     DBuf<uint64_t> tmp;
-    GOD_TRY(tmp.alloc(2 * total, st));  // indexed by the read's anchor offset
-    const size_t smem = kLargeCap * sizeof(uint64_t);
+    if (n_huge) GOD_TRY(tmp.alloc(2 * total, st));  // merge buffers, indexed by the read's anchor offset
+    const size_t smem = 2 * kLargeCap * sizeof(uint64_t) + (kLargeThreads / 32) * 256 * 4 + 256 * 4;
     GOD_CK(cudaFuncSetAttribute(fill_sort_large, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const unsigned grid = (unsigned)std::min<uint64_t>(n_large, (uint64_t)num_sms() * 3);
-    GOD_LAUNCH(fill_sort_large, grid, kLargeThreads, smem, st, sets, src.p, seed_seg.p, read_off.p, llarge.p,
-               (uint32_t)n_large, idx->d_ent, out, tmp.p);
+    const unsigned grid = (unsigned)std::min<uint64_t>(n_large + n_huge, (uint64_t)num_sms() * 3);
+    GOD_LAUNCH(fill_sort_large, grid, kLargeThreads, smem, st, sets, src.p, seed_seg.p, read_off.p, lhuge.p,
+               (uint32_t)n_huge, llarge.p, (uint32_t)n_large, idx->d_ent, out, tmp.p, fill_queue);
   }
   return GOD_OK;
 }
