@@ -9,6 +9,7 @@ There is no CPU fallback: a missing or unloadable library raises.
 from __future__ import annotations
 
 import ctypes as C
+import weakref
 
 import numpy as np
 
@@ -135,6 +136,18 @@ def _opts(stream=None, pa_t=None, via=None, shifts_out=None) -> SeedOpts:
     return o
 
 
+def _owned_anchors(ptr: C.c_void_p, m: int) -> np.ndarray:
+    """Anchor array over a library-allocated host buffer (no copy); the buffer
+    goes back through god_free when the last numpy view of it is released."""
+    L = load()
+    if not m:
+        L.god_free(ptr)
+        return np.zeros(0, np.uint32).view(ANCHOR_DTYPE)
+    buf = (C.c_uint32 * (4 * m)).from_address(ptr.value)
+    weakref.finalize(buf, L.god_free, C.c_void_p(ptr.value))
+    return np.frombuffer(buf, dtype=np.uint32).view(ANCHOR_DTYPE)
+
+
 def god_seed(index: GodIndex, reads, offsets):
     """Sorted anchors of a read batch (host numpy arrays in, structured array out)."""
     reads = _u8(reads)
@@ -144,16 +157,7 @@ def god_seed(index: GodIndex, reads, offsets):
     cnt = C.c_uint64()
     L = load()
     check(L.god_seed(index.h, _ptr(reads), _ptr(offs), n, C.byref(ptr), C.byref(cnt)))
-    m = cnt.value
-    try:
-        if m:
-            buf = (C.c_uint32 * (4 * m)).from_address(ptr.value)
-            arr = np.frombuffer(buf, dtype=np.uint32).copy()
-        else:
-            arr = np.zeros(0, np.uint32)
-    finally:
-        L.god_free(ptr)
-    return arr.view(ANCHOR_DTYPE)
+    return _owned_anchors(ptr, cnt.value)
 
 
 def god_seed_into(index: GodIndex, reads, offsets, out, stream=None, pa_t=None, via=None, shifts_out=None) -> int:
@@ -288,15 +292,10 @@ class GodServer:
         if rc == -6:
             return None
         check(rc)
-        m = cnt.value
-        try:
-            arr = np.frombuffer((C.c_uint32 * (4 * m)).from_address(ptr.value), dtype=np.uint32).copy() if m \
-                else np.zeros(0, np.uint32)
-        finally:
-            L.god_free(ptr)
+        arr = _owned_anchors(ptr, cnt.value)
         if with_latency:
-            return arr.view(ANCHOR_DTYPE), lat.value
-        return arr.view(ANCHOR_DTYPE)
+            return arr, lat.value
+        return arr
 
     def stats(self) -> dict:
         s = ServerStats()

@@ -50,6 +50,47 @@ uint64_t batch_bytes_estimate(const god_index* idx, uint64_t bases, uint64_t n) 
   return (uint64_t)(b * 1.5) + (16ull << 20);
 }
 
+// bounds[j] = first anchor of request j (anchors sorted by batch read id;
+// request j owns batch reads [first[j], first[j + 1])), bounds[m] = n.
+__global__ void request_bounds(const god_anchor* __restrict__ a, uint64_t n, const uint32_t* __restrict__ first,
+                               uint32_t m, uint64_t* __restrict__ bounds) {
+  for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j <= m; j += gridDim.x * blockDim.x) {
+    if (j == m) {
+      bounds[j] = n;
+      continue;
+    }
+    uint64_t lo = 0, hi = n;
+    while (lo < hi) {
+      const uint64_t mid = (lo + hi) >> 1;
+      if (a[mid].read_id < first[j]) lo = mid + 1; else hi = mid;
+    }
+    bounds[j] = lo;
+  }
+}
+
+// Read ids back to each request's own numbering.
+__global__ void rebase_read_ids(god_anchor* __restrict__ a, uint64_t n, const uint32_t* __restrict__ first,
+                                uint32_t m) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t r = a[i].read_id;
+    uint32_t lo = 0, hi = m;                   // largest j with first[j] <= r
+    while (hi - lo > 1) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (first[mid] <= r) lo = mid; else hi = mid;
+    }
+    a[i].read_id = r - first[lo];
+  }
+}
+
+int split_on_device(god_anchor* d_out, uint64_t total, const uint32_t* d_first, uint32_t m, uint64_t* d_bounds,
+                    cudaStream_t st) {
+  GOD_LAUNCH(request_bounds, (m + 128) / 128, 128, 0, st, d_out, total, d_first, m, d_bounds);
+  if (total)
+    GOD_LAUNCH(rebase_read_ids, (unsigned)std::min<uint64_t>((total + 255) / 256, 4096), 256, 0, st, d_out, total,
+               d_first, m);
+  return GOD_OK;
+}
+
 }  // namespace
 
 struct god_server {
@@ -180,9 +221,25 @@ void worker_main(god_server* S, int slot) {
       cap_out = std::max<uint64_t>(total, 1 << 16);
       if (cudaMallocHost(&h_out, cap_out * sizeof(god_anchor)) != cudaSuccess) { h_out = nullptr; cap_out = 0; rc = GOD_ENOMEM; }
     }
+    // request boundaries and per-request read ids on the device, so the
+    // split below is one copy per request
+    const uint32_t m = (uint32_t)batch.size();
+    std::vector<uint64_t> bounds(m + 1, 0);
+    god::DBuf<uint32_t> d_first;
+    god::DBuf<uint64_t> d_bounds;
+    if (rc == GOD_OK) rc = d_first.alloc(m, stream);
+    if (rc == GOD_OK) rc = d_bounds.alloc(m + 1, stream);
+    std::vector<uint32_t> first32(first_read.begin(), first_read.end());
+    if (rc == GOD_OK)
+      rc = cudaMemcpyAsync(d_first.p, first32.data(), m * 4, cudaMemcpyHostToDevice, stream) ? GOD_ECUDA : GOD_OK;
+    if (rc == GOD_OK) rc = split_on_device(d_out, total, d_first.p, m, d_bounds.p, stream);
+    if (rc == GOD_OK)
+      rc = cudaMemcpyAsync(bounds.data(), d_bounds.p, (m + 1) * 8, cudaMemcpyDeviceToHost, stream) ? GOD_ECUDA : GOD_OK;
     if (rc == GOD_OK && total)
       rc = cudaMemcpyAsync(h_out, d_out, total * sizeof(god_anchor), cudaMemcpyDeviceToHost, stream) ? GOD_ECUDA : GOD_OK;
     if (d_out) god::dfree(d_out, stream);
+    d_first.release();
+    d_bounds.release();
     d_reads.release();
     d_offs.release();
     if (cudaStreamSynchronize(stream) != cudaSuccess && rc == GOD_OK) rc = GOD_ECUDA;
@@ -191,19 +248,10 @@ void worker_main(god_server* S, int slot) {
       Request* r = batch[bi];
       r->rc = rc;
       if (rc == GOD_OK) {
-        const uint32_t lo = (uint32_t)first_read[bi], hi = lo + r->n;
-        const god_anchor* b = std::lower_bound(h_out, h_out + total, lo,
-                                               [](const god_anchor& a, uint32_t v) { return a.read_id < v; });
-        const god_anchor* e = std::lower_bound(b, (const god_anchor*)h_out + total, hi,
-                                               [](const god_anchor& a, uint32_t v) { return a.read_id < v; });
-        r->n_result = (uint64_t)(e - b);
+        r->n_result = bounds[bi + 1] - bounds[bi];
         r->result = (god_anchor*)malloc(std::max<uint64_t>(r->n_result, 1) * sizeof(god_anchor));
         if (!r->result) r->rc = GOD_ENOMEM;
-        else
-          for (uint64_t i = 0; i < r->n_result; ++i) {
-            r->result[i] = b[i];
-            r->result[i].read_id -= lo;
-          }
+        else if (r->n_result) memcpy(r->result, h_out + bounds[bi], r->n_result * sizeof(god_anchor));
       }
       r->merged = batch.size() > 1;
       std::vector<uint8_t>().swap(r->reads);
