@@ -276,7 +276,10 @@ typedef struct {
 
 void god_server_config_init(god_server_config *c);
 int god_server_create(const god_index *idx, const god_server_config *cfg, god_server **out);
-/* Queues a copy of the reads (host) and returns a request id. */
+/* Queues a request and returns its id. The reads and offsets stay in the
+ * caller's host memory, which must remain valid and unchanged until
+ * god_server_wait has returned for this request (the offsets are copied at
+ * submit, the read bytes once, into the batch's pinned staging). */
 int god_server_submit(god_server *s, const uint8_t *reads, const uint64_t *offsets, uint32_t n,
                       uint64_t *request_id);
 /* Waits up to timeout_ms (negative = forever) for a request. On GOD_OK the

@@ -275,12 +275,14 @@ class GodServer:
         check(L.god_server_create(index.h, C.byref(cfg), C.byref(h)))
         self.h = h
         self.index = index
+        self._held = {}   # request id -> the arrays the server reads from until its wait returns
 
     def submit(self, reads, offsets) -> int:
         reads = _u8(reads)
         offs = np.ascontiguousarray(offsets, dtype=np.uint64)
         rid = C.c_uint64()
         check(load().god_server_submit(self.h, _ptr(reads), _ptr(offs), offs.size - 1, C.byref(rid)))
+        self._held[rid.value] = (reads, offs)
         return rid.value
 
     def wait(self, request_id: int, timeout_ms: int = -1, with_latency: bool = False):
@@ -291,6 +293,7 @@ class GodServer:
         rc = L.god_server_wait(self.h, request_id, timeout_ms, C.byref(ptr), C.byref(cnt), C.byref(lat))
         if rc == -6:
             return None
+        self._held.pop(request_id, None)
         check(rc)
         arr = _owned_anchors(ptr, cnt.value)
         if with_latency:
@@ -306,6 +309,7 @@ class GodServer:
         if self.h and self.h.value:
             check(load().god_server_destroy(self.h))
             self.h = C.c_void_p(0)
+        self._held.clear()
 
     def __del__(self):
         try:

@@ -28,8 +28,8 @@ using Clock = std::chrono::steady_clock;
 
 struct Request {
   uint64_t id;
-  std::vector<uint8_t> reads;
-  std::vector<uint64_t> offs;   // n + 1, rebased to 0
+  const uint8_t* reads = nullptr;   // the caller's bytes (valid until its wait returns)
+  std::vector<uint64_t> offs;       // n + 1, rebased to 0
   uint32_t n;
   uint64_t bases;
   Clock::time_point t_submit, t_done;
@@ -192,7 +192,7 @@ void worker_main(god_server* S, int slot) {
     if (rc == GOD_OK) {
       uint64_t bo = 0, ro = 0;
       for (Request* r : batch) {
-        memcpy(h_reads + bo, r->reads.data(), r->bases);
+        memcpy(h_reads + bo, r->reads, r->bases);
         for (uint32_t i = 0; i < r->n; ++i) h_offs[ro + i] = bo + r->offs[i];
         first_read.push_back(ro);
         bo += r->bases;
@@ -254,7 +254,6 @@ void worker_main(god_server* S, int slot) {
         else if (r->n_result) memcpy(r->result, h_out + bounds[bi], r->n_result * sizeof(god_anchor));
       }
       r->merged = batch.size() > 1;
-      std::vector<uint8_t>().swap(r->reads);
     }
     {
       std::lock_guard<std::mutex> lk(S->mu);
@@ -325,7 +324,7 @@ int god_server_submit(god_server* S, const uint8_t* reads, const uint64_t* offse
     r->offs[i] = offsets[i] - b0;
   }
   r->bases = n ? offsets[n] - b0 : 0;
-  r->reads.assign(reads + b0, reads + b0 + r->bases);
+  r->reads = reads + b0;
   r->t_submit = Clock::now();
   {
     std::lock_guard<std::mutex> lk(S->mu);
