@@ -242,7 +242,8 @@ uint64_t god_launch_count(void);
  * without timing); 0 switches timing off. god_prof_report writes a JSON object
  * {"kernel": [launches, total_ms, algorithmic_bytes, units], ...} (bytes and
  * units are filled in for the sketch kernel: patterned bases read plus 16-byte
- * minimizer records written; and for the lookups: 32 bytes per probe) of
+ * minimizer records written; and for the lookups: the record, its results
+ * and the table words and offsets a probe reads) of
  * everything timed since the last
  * reset into buf (NUL-terminated) and returns 0, or returns the needed size
  * when cap is too small. Reading the report waits for the timed launches. */

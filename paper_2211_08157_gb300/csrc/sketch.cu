@@ -1,5 +1,5 @@
 // Fused seed extraction: sparsify + 2-bit code + canonical Wang hash +
-// (w,k)-minimizer selection + ordered compaction, in one persistent kernel.
+// (w,k)-minimizer selection, in one persistent kernel.
 //
 // The method (Sec. 3.1, Sec. 3.6.1) extracts seeds from a patterned sequence:
 // keep the bases under the 1s of the repeating diet pattern, code them in 2
@@ -7,25 +7,29 @@
 // hash, and keep, in every window of w consecutive k-mers, every k-mer whose
 // hash is the window minimum. The paper vectorises this over 8 k-mers with
 // AVX-512; here every patterned sequence (the reference, or one read at one
-// shift) is a segment of a virtual stream, and CTAs take fixed-size tiles of
-// that stream from an atomic ticket, so long and short sequences load-balance
-// by construction.
+// shift) is a segment of a virtual stream, and CTAs stride over fixed-size
+// tiles of that stream, so long and short sequences load-balance by
+// construction.
 //
 // Per tile of T owned k-mer positions [A, A + T):
-//  1. gather the 2-bit codes of stream positions [A - w + 1, A + T + w + k - 2)
-//     into shared memory; the kept-base arithmetic is closed form
-//     (orig = s + p * (j / x) + off[j mod x]), so no scan is needed; a
-//     separator position after each segment reads as N;
-//  2. roll forward / reverse-complement codes per thread over a contiguous
-//     chunk and hash the canonical code -> key + 1 (0 marks a k-mer with N,
-//     all-ones marks a palindrome, which is never chosen);
+//  1. gather the bases of stream positions [A - w + 1, A + T + w + k - 2)
+//     eight per thread through a byte -> 2-bit code table and pack them into
+//     64-bit forward and complement words in shared memory; the kept-base
+//     arithmetic is closed form (orig = s + p * (j / x) + off[j mod x]), so no
+//     scan is needed; a separator position after each segment reads as N;
+//  2. four consecutive k-mers per thread from one 64-bit window of each
+//     strand; the canonical code is hashed -> key + 1 (0 marks a k-mer with
+//     N, all-ones marks a palindrome, which is never chosen);
 //  3. window minima M[i] = min(key[i .. i + w - 1]) by van Herk / Gil-Werman
-//     block prefix/suffix minima;
+//     block suffix minima (registers) and the next block's prefix minima
+//     (shuffles), one warp per sub-tile;
 //  4. position j is a minimizer iff key[j] equals max(M[j - w + 1 .. j]) (every
 //     window containing j has minimum <= key[j], so j is some window's minimum
 //     exactly when the largest of those minima equals key[j]);
-//  5. ordered compaction with a decoupled look-back over tile tickets, so the
-//     output is in stream order (segment, position) with no second pass.
+//  5. records of the selected positions, in order, into the sub-tile's staging
+//     slots (a scan of the per-sub-tile counts orders them), or, for the
+//     allocation-free entry point, at their final place after a decoupled
+//     look-back over sub-tiles taken from a ticket.
 #include <algorithm>
 #include <map>
 #include <mutex>
