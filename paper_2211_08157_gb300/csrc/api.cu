@@ -245,10 +245,29 @@ void register_host_array(void* p) {
   if (p) reg_add(p, Kind::HostArray, 0);
 }
 
-// Copies `bytes` of a host-or-device input into a device buffer (or aliases it).
+// Device address of page-locked host memory (readable and writable by kernels
+// over the host link), null for any other pointer.
+static void* pinned_host_device_ptr(const void* p) {
+  if (!p) return nullptr;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
+// A host-or-device input as a device-readable pointer: device memory and
+// page-locked host memory are used in place (kernels read the latter over the
+// host link, once, while they compute), other host memory is copied into a
+// device buffer.
 static int to_device(const void* p, size_t bytes, DBuf<uint8_t>& hold, const void** dp, cudaStream_t st) {
   if (bytes == 0 || is_device_ptr(p)) {
     *dp = p;
+    return GOD_OK;
+  }
+  if (void* mapped = pinned_host_device_ptr(p)) {
+    *dp = mapped;
     return GOD_OK;
   }
   GOD_TRY(hold.alloc(bytes, st));
@@ -550,11 +569,12 @@ static int seed_common(const god_index* idx, const uint8_t* reads, const uint64_
     GOD_CK(cudaMemcpyAsync(&bytes, offsets + n, 8, cudaMemcpyDeviceToHost, st));
     GOD_CK(cudaStreamSynchronize(st));
   } else {
-    for (uint32_t i = 0; i < n; ++i)
-      if (offsets[i + 1] < offsets[i] || offsets[i + 1] - offsets[i] >= (1ULL << 31)) {
-        set_error("offsets must be non-decreasing and each read < 2^31 bytes");
-        return GOD_EINVAL;
-      }
+    // the offsets themselves are checked on the device (make_pa_segments);
+    // only the total is needed here, to size the copy of the reads
+    if (offsets[n] < offsets[0]) {
+      set_error("offsets must be non-decreasing and each read < 2^31 bytes");
+      return GOD_EINVAL;
+    }
     bytes = offsets[n];
     GOD_TRY(to_device(offsets, (uint64_t)(n + 1) * 8, hold_off, &doff, st));
   }
@@ -588,6 +608,8 @@ int god_seed_into(const god_index* idx, const uint8_t* reads, const uint64_t* of
   god_seed_opts_init(&o);
   if (opts) o = *opts;
   cudaStream_t st = (cudaStream_t)o.stream;
+  // a host output (page-locked or not) is filled by one copy after the device
+  // pass: the fill kernels writing over the host link measured slower
   if (out && is_device_ptr(out)) {
     int rc = seed_common(idx, reads, offsets, n, o, nullptr, n_anchors, out, cap);
     if (rc == GOD_OK) GOD_CK(cudaStreamSynchronize(st));
