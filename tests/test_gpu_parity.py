@@ -81,6 +81,24 @@ def test_sketch_low_complexity(god):
         assert np.array_equal(gk, ok) and np.array_equal(gp.astype(np.uint64), op), (k, w)
 
 
+def test_sketch_every_byte_value(god):
+    """Bytes other than ACGT/acgt (all 256 values, random positions) read as N
+    under the word-wise gather (patterns 10, 110, 1, 1110) and the byte-wise
+    one (1000101001), at every shift."""
+    rng = np.random.default_rng(41)
+    seq = rand_bytes(rng, 24_000, lower=0.2)
+    hit = rng.random(seq.size) < 0.01
+    seq[hit] = rng.integers(0, 256, int(hit.sum()))
+    seq[1000:1256] = np.arange(256)
+    seq[5000:5512] = np.repeat(np.arange(256), 2)
+    for P, k, w in [("10", 21, 11), ("110", 19, 19), ("1", 15, 10), ("1110", 17, 9), ("1000101001", 12, 7)]:
+        for s in range(len(P)):
+            gk, gp, gz = god.god_sketch(seq, P, s, k, w)
+            ok, op, oz, _ = oracle.minimizers(seq, P, s, k, w)
+            assert np.array_equal(gk, ok) and np.array_equal(gp.astype(np.uint64), op), (P, s)
+            assert np.array_equal(gz.astype(np.uint32), oz), (P, s)
+
+
 # ----------------------------------------------------------------- index
 @pytest.mark.parametrize("P,k,w,occ", [("10", 21, 11, 500), ("110", 19, 19, 3), ("1", 15, 10, 2), ("1010", 13, 6, 1)])
 def test_index_matches_oracle(god, P, k, w, occ):
@@ -176,6 +194,29 @@ def test_seed_reads_with_n_and_edge_lengths(god):
     offs = np.array(offs, np.uint64)
     _seed_compare(god, ref, reads, offs, "110", 19, 9, 500, t=4)
     _seed_compare(god, ref, reads, offs, "10", 21, 11, 500, t=32)
+
+
+def test_seed_short_segments_and_odd_bytes(god):
+    """Reads of 0-40 and 150 bases with non-ACGT bytes: chunks that straddle
+    one, two or more segment ends and separators next to N."""
+    rng = np.random.default_rng(23)
+    ref = synth.reference(100_000, 14)
+    parts, offs = [], [0]
+    for i in range(3000):
+        L = int(rng.choice([0, 1, 2, 7, 8, 9, 15, 16, 17, 23, 33, 40, 150]))
+        s = int(rng.integers(0, ref.size - L)) if L else 0
+        r = ref[s:s + L].copy()
+        if L and i % 4 == 0:
+            r[rng.integers(0, L, max(1, L // 30))] = rng.integers(0, 256, max(1, L // 30))
+        if L and i % 3 == 0:
+            r = r | np.uint8(0x20) * (rng.random(L) < 0.3).astype(np.uint8)
+        parts.append(r)
+        offs.append(offs[-1] + L)
+    reads = np.concatenate(parts)
+    offs = np.array(offs, np.uint64)
+    _seed_compare(god, ref, reads, offs, "10", 9, 3, 200, t=0)
+    _seed_compare(god, ref, reads, offs, "110", 10, 4, 200, t=0)
+    _seed_compare(god, ref, reads, offs, "1", 11, 3, 200, t=0)
 
 
 def test_seed_long_anchor_lists(god):
