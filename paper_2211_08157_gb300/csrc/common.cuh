@@ -243,9 +243,11 @@ struct DeviceIndex {           // what lookup kernels need, by value
   const uint32_t* start;       // n_keys + 1
   const uint64_t* ent;         // (pos << 1) | z
   // hash table: 2^ht_lc slots of one word [key >> ht_lc | displacement from
-  // the home slot (ht_db bits) | rank in keys (ht_rb bits)], ~0 when empty
+  // the home slot (ht_db bits) | field (ht_rb bits)], ~0 when empty. The
+  // field is start << ht_cb | count when ht_cb > 0 (payload slots), else the
+  // key's rank in keys
   const uint64_t* ht;
-  uint32_t ht_lc, ht_db, ht_rb;
+  uint32_t ht_lc, ht_db, ht_rb, ht_cb;
   uint64_t n_keys;
   const RmiLeaf* leaves;       // null without a learned index
   const RmiRoot* root;         // device copy
@@ -268,7 +270,7 @@ struct god_index {
   uint64_t* d_ent;
   uint64_t* d_ht;
   uint64_t ht_cap;
-  uint32_t ht_lc, ht_db, ht_rb;
+  uint32_t ht_lc, ht_db, ht_rb, ht_cb;
   god_params params;
   // learned index
   int has_rmi;

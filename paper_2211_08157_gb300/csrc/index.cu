@@ -91,19 +91,20 @@ __global__ void emit_runs(const uint64_t* __restrict__ keys, const V* __restrict
   }
 }
 
-// Hash table insert of key rank r (linear probing, one CAS per probe). A
-// displacement past the field's range sets *overflow (the caller rebuilds a
-// larger table).
-__global__ void ht_insert(const uint64_t* __restrict__ keys, uint64_t U, uint64_t* ht, uint32_t lc, uint32_t db,
-                          uint32_t rb, int* overflow) {
+// Hash table insert of key rank r (linear probing, one CAS per probe); the
+// slot field is start << cb | count (cb > 0) or r. A displacement past the
+// field's range sets *overflow (the caller rebuilds a larger table).
+__global__ void ht_insert(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ start, uint64_t U,
+                          uint64_t* ht, uint32_t lc, uint32_t db, uint32_t rb, uint32_t cb, int* overflow) {
   const uint64_t mask = (1ULL << lc) - 1;
   const uint64_t maxd = (1ULL << db) - 2;
   for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < U; r += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t key = keys[r];
     const uint64_t h = key & mask, q = key >> lc;
+    const uint64_t field = cb ? ((uint64_t)start[r] << cb) | (start[r + 1] - start[r]) : r;
     bool placed = false;
     for (uint64_t d = 0; d <= maxd; ++d) {
-      const unsigned long long word = (unsigned long long)((((q << db) | d) << rb) | r);
+      const unsigned long long word = (unsigned long long)((((q << db) | d) << rb) | field);
       unsigned long long* slot = reinterpret_cast<unsigned long long*>(ht + ((h + d) & mask));
       if (atomicCAS(slot, (unsigned long long)kEmptyKey, word) == kEmptyKey) {
         placed = true;
@@ -140,6 +141,7 @@ DeviceIndex device_view(const god_index* idx, int via) {
   d.ht_lc = idx->ht_lc;
   d.ht_db = idx->ht_db;
   d.ht_rb = idx->ht_rb;
+  d.ht_cb = idx->ht_cb;
   d.n_keys = idx->n_keys;
   d.leaves = (via == 1 && idx->has_rmi) ? idx->d_leaves : nullptr;
   d.root = (via == 1 && idx->has_rmi) ? idx->d_root : nullptr;
@@ -246,10 +248,15 @@ int build_index_device(god_index* idx, const uint8_t* d_ref, uint64_t len, cudaS
   else
     GOD_TRY(sort_and_emit<uint64_t>(idx, S, n, st, okeys, ostart, oent, &U, &E));
   // hash table at load <= 1/2; the slot word splits 64 bits into the quotient
-  // (2k - lc bits), the rank (rb bits) and the displacement (the rest, >= 9
-  // bits for k <= 28 since 2^lc >= 2U)
-  uint32_t rb = 1;
-  while (rb < 63 && (1ULL << rb) < U) ++rb;
+  // (2k - lc bits), the field (rb bits) and the displacement (the rest). The
+  // field is the key's (start, count) when that leaves at least 8
+  // displacement bits, else its rank (then >= 9 displacement bits for k <= 28
+  // since 2^lc >= 2U)
+  uint32_t rank_bits = 1;
+  while (rank_bits < 63 && (1ULL << rank_bits) < U) ++rank_bits;
+  uint32_t start_bits = 1, count_bits = 1;
+  while (start_bits < 40 && (1ULL << start_bits) < E) ++start_bits;
+  while (count_bits < 32 && (1ULL << count_bits) <= std::min<uint64_t>(idx->max_occ, E)) ++count_bits;
   uint32_t lc = 4;
   while ((1ULL << lc) < 2 * U) ++lc;
   DBuf<uint64_t> ht;
@@ -257,6 +264,9 @@ int build_index_device(god_index* idx, const uint8_t* d_ref, uint64_t len, cudaS
   GOD_TRY(ovf.alloc(1, st));
   for (;; ++lc) {
     const uint32_t qb = 2 * idx->k > (int)lc ? 2 * idx->k - lc : 0;
+    const bool payload = qb + start_bits + count_bits + 8 <= 64;
+    const uint32_t rb = payload ? start_bits + count_bits : rank_bits;
+    const uint32_t cb = payload ? count_bits : 0;
     const uint32_t db = 64 - qb - rb;
     if (qb + rb > 62 || lc > 40) {
       set_error("index: hash table does not fit");
@@ -267,7 +277,7 @@ int build_index_device(god_index* idx, const uint8_t* d_ref, uint64_t len, cudaS
     GOD_CK(cudaMemsetAsync(ht.p, 0xFF, cap * sizeof(uint64_t), st));
     GOD_CK(cudaMemsetAsync(ovf.p, 0, sizeof(int), st));
     if (U) GOD_LAUNCH(ht_insert, std::min<unsigned>(blocks_for(U), (unsigned)num_sms() * 32), kThreads, 0, st,
-                      okeys.p, U, ht.p, lc, db, rb, ovf.p);
+                      okeys.p, ostart.p, U, ht.p, lc, db, rb, cb, ovf.p);
     int h_ovf = 0;
     GOD_CK(cudaMemcpyAsync(&h_ovf, ovf.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     GOD_CK(cudaStreamSynchronize(st));
@@ -275,6 +285,7 @@ int build_index_device(god_index* idx, const uint8_t* d_ref, uint64_t len, cudaS
       idx->ht_lc = lc;
       idx->ht_db = db;
       idx->ht_rb = rb;
+      idx->ht_cb = cb;
       idx->ht_cap = cap;
       break;
     }

@@ -37,17 +37,20 @@ __device__ __forceinline__ int64_t rmi_leaf_pred(float slope, float icept, uint6
 
 // Open-addressing probe. Linear probing from the home slot key mod 2^lc; a
 // slot holds the key's quotient key >> lc, its displacement d from the home
-// slot and its rank in keys[]. The home slot is implied by the probe
-// position, so (quotient, d) identifies the whole key and a match is exact.
+// slot and a field: the key's (start, count) in the entry array when those
+// fit (payload slots, one memory access per lookup), else its rank in keys[]
+// (the offsets then come from start[rank], start[rank + 1]). The home slot is
+// implied by the probe position, so (quotient, d) identifies the whole key
+// and a match is exact.
 constexpr uint64_t kNoRank = ~0ULL;
 
 __device__ __forceinline__ uint64_t ht_home_word(const DeviceIndex& di, uint64_t key) {
   return __ldg(di.ht + (key & ((1ULL << di.ht_lc) - 1)));
 }
 
-// Rank of key in keys[] (kNoRank when absent), given the word at its home
-// slot (loaded by the caller, so that several probes can be in flight).
-__device__ __forceinline__ uint64_t ht_rank(const DeviceIndex& di, uint64_t key, uint64_t w0) {
+// Slot field of key (kNoRank when absent), given the word at its home slot
+// (loaded by the caller, so that several probes can be in flight).
+__device__ __forceinline__ uint64_t ht_field(const DeviceIndex& di, uint64_t key, uint64_t w0) {
   const uint32_t lc = di.ht_lc, db = di.ht_db, rb = di.ht_rb;
   const uint64_t mask = (1ULL << lc) - 1, h = key & mask;
   const uint64_t q = key >> lc;
@@ -70,9 +73,15 @@ __device__ __forceinline__ uint64_t rank_payload(const DeviceIndex& di, uint64_t
   return (uint64_t)s | ((uint64_t)(e - s) << 32);
 }
 
+// start | count << 32 of a slot field (0 for kNoRank).
+__device__ __forceinline__ uint64_t field_payload(const DeviceIndex& di, uint64_t f) {
+  if (di.ht_cb == 0 || f == kNoRank) return rank_payload(di, f);
+  return (f >> di.ht_cb) | ((f & ((1ULL << di.ht_cb) - 1)) << 32);
+}
+
 // start | count << 32 of key, 0 when absent.
 __device__ __forceinline__ uint64_t ht_find(const DeviceIndex& di, uint64_t key) {
-  return rank_payload(di, ht_rank(di, key, ht_home_word(di, key)));
+  return field_payload(di, ht_field(di, key, ht_home_word(di, key)));
 }
 
 // Learned-index lookup in steps, so that a caller can keep several keys in

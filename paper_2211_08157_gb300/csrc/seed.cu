@@ -668,9 +668,9 @@ __global__ void __launch_bounds__(kT) compact_lookup(const MinRec* __restrict__ 
 #pragma unroll
         for (int u = 0; u < U; ++u) w[u] = ok[u] ? ht_home_word(di, key[u]) : kEmptyKey;
 #pragma unroll
-        for (int u = 0; u < U; ++u) rk[u] = ok[u] ? ht_rank(di, key[u], w[u]) : kNoRank;
+        for (int u = 0; u < U; ++u) rk[u] = ok[u] ? ht_field(di, key[u], w[u]) : kNoRank;
 #pragma unroll
-        for (int u = 0; u < U; ++u) pay[u] = rank_payload(di, rk[u]);
+        for (int u = 0; u < U; ++u) pay[u] = field_payload(di, rk[u]);
       }
 #pragma unroll
       for (int u = 0; u < U; ++u) {
