@@ -238,6 +238,8 @@ __device__ __forceinline__ void cswap(uint64_t& a, uint64_t& b, bool up) {
   b = up ? hi : lo;
 }
 
+constexpr int kFillBatch = 4;
+
 __global__ void __launch_bounds__(kT) fill_sort_tiny(RecSets sets, const uint32_t* __restrict__ src,
                                                      const uint32_t* __restrict__ seed_seg,
                                                      const uint64_t* __restrict__ read_off,
@@ -255,16 +257,28 @@ __global__ void __launch_bounds__(kT) fill_sort_tiny(RecSets sets, const uint32_
 #pragma unroll
     for (int q = 0; q < kTinyCap; ++q) v[q] = ~0ULL;
     uint32_t fill = 0;
-    for (uint32_t r = 0; r < cnt; ++r) {
-      const uint64_t sc = S.sc[beg + r];
-      const uint32_t c = (uint32_t)(sc >> 32);
-      if (!c) continue;
-      const uint32_t pzv = S.pz[beg + r];
-      const uint32_t start = (uint32_t)sc;
-      for (uint32_t e = 0; e < c; ++e, ++fill) {
-        const uint64_t key = anchor_key(__ldg(ent + start + e), pzv >> 1, pzv & 1u);
+    // kFillBatch records at a time: their lookups, then their positions and
+    // first entries (most keys occur once), so the dependent loads overlap
+    for (uint32_t r0 = 0; r0 < cnt; r0 += kFillBatch) {
+      uint64_t sc[kFillBatch], e0[kFillBatch];
+      uint32_t pzv[kFillBatch];
 #pragma unroll
-        for (int q = 0; q < kTinyCap; ++q) v[q] = (q == (int)fill) ? key : v[q];
+      for (int u = 0; u < kFillBatch; ++u) sc[u] = r0 + u < cnt ? S.sc[beg + r0 + u] : 0;
+#pragma unroll
+      for (int u = 0; u < kFillBatch; ++u) {
+        const bool hit = (sc[u] >> 32) != 0;
+        pzv[u] = hit ? S.pz[beg + r0 + u] : 0u;
+        e0[u] = hit ? __ldg(ent + (uint32_t)sc[u]) : 0;
+      }
+#pragma unroll
+      for (int u = 0; u < kFillBatch; ++u) {
+        const uint32_t c = (uint32_t)(sc[u] >> 32);
+        for (uint32_t e = 0; e < c; ++e, ++fill) {
+          const uint64_t en = e ? __ldg(ent + (uint32_t)sc[u] + e) : e0[u];
+          const uint64_t key = anchor_key(en, pzv[u] >> 1, pzv[u] & 1u);
+#pragma unroll
+          for (int q = 0; q < kTinyCap; ++q) v[q] = (q == (int)fill) ? key : v[q];
+        }
       }
     }
 #pragma unroll
