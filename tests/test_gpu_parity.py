@@ -82,9 +82,8 @@ def test_sketch_low_complexity(god):
 
 
 def test_sketch_every_byte_value(god):
-    """Bytes other than ACGT/acgt (all 256 values, random positions) read as N
-    under the word-wise gather (patterns 10, 110, 1, 1110) and the byte-wise
-    one (1000101001), at every shift."""
+    """Bytes other than ACGT/acgt (all 256 values, at random positions) read as
+    N, for contiguous and spread-out patterns at every shift."""
     rng = np.random.default_rng(41)
     seq = rand_bytes(rng, 24_000, lower=0.2)
     hit = rng.random(seq.size) < 0.01
@@ -100,7 +99,10 @@ def test_sketch_every_byte_value(god):
 
 
 # ----------------------------------------------------------------- index
-@pytest.mark.parametrize("P,k,w,occ", [("10", 21, 11, 500), ("110", 19, 19, 3), ("1", 15, 10, 2), ("1010", 13, 6, 1)])
+# hash slots hold (start, count) where the fields fit (k <= 21 here) and the
+# key's rank otherwise (k = 28: a 40-bit quotient leaves too few bits)
+@pytest.mark.parametrize("P,k,w,occ", [("10", 21, 11, 500), ("110", 19, 19, 3), ("1", 15, 10, 2), ("1010", 13, 6, 1),
+                                       ("10", 28, 11, 500), ("1", 28, 5, 2**32 - 1), ("1", 15, 10, 2**32 - 1)])
 def test_index_matches_oracle(god, P, k, w, occ):
     ref = synth.reference(300_000, 7, synth.RepeatModel(20, 300, 900, False, 0.0, 0.02, 0.3))
     idx = god.god_build_index(ref, P, k, w, occ)
@@ -217,6 +219,16 @@ def test_seed_short_segments_and_odd_bytes(god):
     _seed_compare(god, ref, reads, offs, "10", 9, 3, 200, t=0)
     _seed_compare(god, ref, reads, offs, "110", 10, 4, 200, t=0)
     _seed_compare(god, ref, reads, offs, "1", 11, 3, 200, t=0)
+
+
+def test_seed_rank_slots(god):
+    """k = 28: the index's hash slots hold ranks (no room for the entry range),
+    so lookups go through the offsets array."""
+    ref = synth.reference(300_000, 15, synth.RepeatModel(20, 300, 900, False, 0.0, 0.02, 0.3))
+    lens = synth.LengthModel("fixed", fixed=150)
+    reads, offs, _ = synth.reads(ref, 2000, lens, synth.ErrorModel(0.002, 1, 1, 1), 15)
+    _seed_compare(god, ref, reads, offs, "10", 28, 11, 500)
+    _seed_compare(god, ref, reads, offs, "1", 28, 9, 3)
 
 
 def test_seed_long_anchor_lists(god):
