@@ -262,12 +262,16 @@ static void* pinned_host_device_ptr(const void* p) {
 // host link, once, while they compute), other host memory is copied into a
 // device buffer.
 static int to_device(const void* p, size_t bytes, DBuf<uint8_t>& hold, const void** dp, cudaStream_t st) {
-  if (bytes == 0 || is_device_ptr(p)) {
+  if (is_device_ptr(p)) {
     *dp = p;
     return GOD_OK;
   }
   if (void* mapped = pinned_host_device_ptr(p)) {
     *dp = mapped;
+    return GOD_OK;
+  }
+  if (bytes == 0) {   // nothing is read through it
+    *dp = p;
     return GOD_OK;
   }
   GOD_TRY(hold.alloc(bytes, st));
@@ -566,8 +570,11 @@ static int seed_common(const god_index* idx, const uint8_t* reads, const uint64_
   uint64_t bytes = 0;
   if (is_device_ptr(offsets)) {
     doff = offsets;
-    GOD_CK(cudaMemcpyAsync(&bytes, offsets + n, 8, cudaMemcpyDeviceToHost, st));
-    GOD_CK(cudaStreamSynchronize(st));
+    // the total is needed only to copy reads from pageable host memory
+    if (!is_device_ptr(reads) && !pinned_host_device_ptr(reads)) {
+      GOD_CK(cudaMemcpyAsync(&bytes, offsets + n, 8, cudaMemcpyDeviceToHost, st));
+      GOD_CK(cudaStreamSynchronize(st));
+    }
   } else {
     // the offsets themselves are checked on the device (make_pa_segments);
     // only the total is needed here, to size the copy of the reads
