@@ -473,12 +473,30 @@ def main():
                    "share": v[1] / sum(x[1] for x in prof_all.values())} for k, v in
                sorted(prof_all.items(), key=lambda kv: -kv[1][1])}
 
-    # ---- seed-only throughput with a resident index (hash and learned)
+    # ---- index build alone, then seed-only throughput with a resident index
+    # (hash and learned; the learned build includes training its model)
     seed_only = {}
+    index_build = {}
     if not args.no_compare:
         for nm, kd in (("hash", god.GOD_INDEX_HASH), ("learned", god.GOD_INDEX_LEARNED)):
             prm = god.god_params_init(index_kind=kd, pa_t=wl.t)
-            idx = god.god_build_index(d_ref, wl.pattern, wl.k, wl.w, wl.max_occ, params=prm, stream=stream)
+            bt = []
+            idx = None
+            for _ in range(3):
+                if idx is not None:
+                    idx.close()
+                with torch.cuda.stream(stream):
+                    flush.zero_()
+                stream.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                idx = god.god_build_index(d_ref, wl.pattern, wl.k, wl.w, wl.max_occ, params=prm, stream=stream)
+                e1.record(stream)
+                e1.synchronize()
+                bt.append(e0.elapsed_time(e1))
+            index_build[nm] = {"ref_bases_per_s": float(ref.size) / (statistics.mean(bt) / 1e3),
+                               "ms": statistics.mean(bt)}
             god.god_seed_into(idx, d_reads, d_offs, d_out, stream=stream)
             tt = []
             for _ in range(3):
@@ -590,7 +608,7 @@ def main():
             "gpu_launches": int(launches),
             "roofline": roof, "sketch_roofline": sketch_roof, "kernels": kernels,
             "kernels_note": f"per-step means over {prof_steps} extra steps with every launch timed by CUDA events",
-            "seed_only_resident_index": seed_only, "serving": serving, "e2e": e2e, "cpu_baseline": cpu,
+            "seed_only_resident_index": seed_only, "index_build_resident_reference": index_build, "serving": serving, "e2e": e2e, "cpu_baseline": cpu,
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)
