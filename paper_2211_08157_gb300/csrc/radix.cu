@@ -5,7 +5,7 @@
 // CTA of a fixed grid (a few per SM) owns one contiguous range of the input.
 // A pass is three launches: every CTA counts the digits of its range, one CTA
 // per digit turns that digit's counts into exclusive offsets over the ranges,
-// and every CTA (adding the totals of the smaller digits) walks its range again in tiles of 4096 pairs, ranking each tile
+// and every CTA (adding the totals of the smaller digits) walks its range again in tiles of 2048 pairs, ranking each tile
 // stably (warp ballots per digit bit give the lanes with an equal digit, then
 // per-warp counters), staging it in shared memory in digit order and writing
 // each digit run at its running offset. No CTA waits on another, so the time
@@ -21,8 +21,8 @@ namespace {
 
 constexpr int kRsThreads = 256;
 constexpr int kRsWarps = kRsThreads / 32;
-constexpr int kRsRounds = 16;                        // items per lane and tile
-constexpr int kRsTile = kRsThreads * kRsRounds;      // 4096 items per tile
+constexpr int kRsRounds = 8;                         // items per lane and tile
+constexpr int kRsTile = kRsThreads * kRsRounds;      // 2048 items per tile
 constexpr int kRsMaxBins = 256;
 constexpr int kRsScanThreads = 1024;
 
@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(kRsScanThreads) rs_scan_rows(uint32_t* cnt, in
 }
 
 template <typename V>
-__global__ void __launch_bounds__(kRsThreads, 3) rs_scatter(const uint64_t* __restrict__ keys_in,
+__global__ void __launch_bounds__(kRsThreads, 4) rs_scatter(const uint64_t* __restrict__ keys_in,
                                                          const V* __restrict__ vals_in,
                                                          uint64_t* __restrict__ keys_out,
                                                          V* __restrict__ vals_out, uint64_t n, int shift,
