@@ -216,6 +216,28 @@ def test_minimizers_brute_force(trial):
     assert oracle_set(seq, P, s, k, w) == brute_minimizers(seq, P, s, k, w)
 
 
+def test_any_other_byte_reads_as_n():
+    """Sec. 3.6.1 alphabet: A, C, G, T in either case are bases; every other
+    byte value (all 256 are planted) breaks k-mers exactly like N."""
+    rng = np.random.default_rng(3)
+    seq = synth.ACGT[rng.integers(0, 4, 6000)].copy()
+    lower = rng.random(seq.size) < 0.1
+    seq[lower] |= 0x20
+    others = np.array([b for b in range(256) if b not in b"ACGTacgt"], dtype=np.uint8)
+    hit = rng.random(seq.size) < 0.02
+    seq[hit] = rng.choice(others, int(hit.sum()))
+    seq[3000:3248] = others
+    canon = seq.copy()
+    canon[np.isin(canon, others)] = ord("N")
+    canon[np.isin(canon, np.frombuffer(b"acgt", np.uint8))] -= 0x20
+    for P, k, w in [("1", 15, 10), ("10", 21, 11), ("110", 19, 19), ("1101", 9, 4)]:
+        for s in range(len(P)):
+            a = oracle.minimizers(seq, P, s, k, w)
+            b = oracle.minimizers(canon, P, s, k, w)
+            for x, y in zip(a[:3], b[:3]):
+                assert np.array_equal(x, y), (P, s)
+
+
 def test_minimizers_even_k_palindromes():
     # ACGT is its own reverse complement (k = 4): it keeps its window slot but is
     # never a minimizer.
