@@ -59,3 +59,25 @@ def test_invalid_arguments_rejected_before_device_work():
     cnt = C.c_uint64()
     assert L.god_sketch(ref.ctypes.data, ref.size, b"1x", 0, 15, 10, None, None, None, 0, C.byref(cnt), None) == -1
     L.god_free(None)  # ignored
+
+
+def test_seeding_entry_points_reject_null_arguments():
+    """Null index, output or input pointers are argument errors, returned before
+    any device work (include/god.h: the library never aborts)."""
+    L = _lib.load()
+    reads = np.frombuffer(b"ACGT" * 40, dtype=np.uint8)
+    offs = np.array([0, 80, 160], dtype=np.uint64)
+    anchors = C.c_void_p()
+    n = C.c_uint64()
+    assert L.god_seed(None, reads.ctypes.data, offs.ctypes.data, 2, C.byref(anchors), C.byref(n)) == -1
+    assert anchors.value is None
+    assert L.god_seed(None, reads.ctypes.data, offs.ctypes.data, 2, None, C.byref(n)) == -1
+    out = np.zeros((16, 4), np.uint32)
+    assert L.god_seed_into(None, reads.ctypes.data, offs.ctypes.data, 2, out.ctypes.data, 16, C.byref(n), None) == -1
+    assert L.god_seed_device(None, reads.ctypes.data, offs.ctypes.data, 2, None, C.byref(n), None) == -1
+    server = C.c_void_p()
+    assert L.god_server_create(None, None, C.byref(server)) == -1
+    keys = np.zeros(4, np.uint64)
+    cnt = np.zeros(4, np.uint32)
+    first = np.zeros(4, np.uint64)
+    assert L.god_index_lookup(None, keys.ctypes.data, 4, 0, cnt.ctypes.data, first.ctypes.data, None) == -1
