@@ -238,6 +238,8 @@ __device__ __forceinline__ void cswap(uint64_t& a, uint64_t& b, bool up) {
   b = up ? hi : lo;
 }
 
+// Records whose loads a tiny-list thread keeps in flight (2,000,000 x 150 bp
+// reads: 1, 2, 4, 8 records took 0.38, 0.32, 0.29, 0.33 ms per batch).
 constexpr int kFillBatch = 4;
 
 __global__ void __launch_bounds__(kT) fill_sort_tiny(RecSets sets, const uint32_t* __restrict__ src,
