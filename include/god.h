@@ -196,17 +196,20 @@ int god_sketch(const uint8_t *seq, uint64_t len, const char *pattern, uint32_t s
  *   d_seq    device memory, len bytes (host pointers are rejected: copying
  *            them would need a device buffer).
  *   d_out    device memory for cap records {key, pos, z} (16 bytes each), in
- *            ascending patterned position.
+ *            ascending patterned position; the address must be a multiple of
+ *            16 bytes (records are written as 16-byte stores), otherwise
+ *            GOD_EINVAL is returned before any work.
  *   *n_out   the number of minimizers; when it exceeds cap, only the first cap
  *            records are written and GOD_ERANGE is returned.
  * Sequences whose patterned length (under pattern and shift) exceeds
  * GOD_NOALLOC_MAX_PATTERNED are rejected with GOD_EINVAL before any work.
  * The first call on a device looks up the scratch array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture. All calls on a device share the array and each
- * call clears what it needs at its start, so calls that overlap on the GPU
- * (e.g. on two streams) race: serialise them. The stream is synchronised
- * before the call returns. */
+ * (cudaGetSymbolAddress) with that device current and caches it. All calls on
+ * a device share the array and each call clears what it needs at its start,
+ * so calls that overlap on the GPU (e.g. on two streams) race: serialise
+ * them. Every call reads its count back and synchronises its stream before it
+ * returns, so it must not be called while that stream is being captured.
+ * On GOD_ETIMEOUT (a bounded device wait gave up) *n_out stays 0. */
 typedef struct {
   uint64_t key;
   uint32_t pos;

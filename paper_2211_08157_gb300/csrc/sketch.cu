@@ -1166,6 +1166,11 @@ extern "C" int god_sketch_noalloc(const uint8_t* d_seq, uint64_t len, const char
     set_error("god_sketch_noalloc: patterned length exceeds GOD_NOALLOC_MAX_PATTERNED");
     return GOD_EINVAL;
   }
+  // records are written as 16-byte vector stores
+  if (cap && (reinterpret_cast<uintptr_t>(d_out) & 15u) != 0) {
+    set_error("god_sketch_noalloc: d_out must be 16-byte aligned");
+    return GOD_EINVAL;
+  }
   if ((len && !is_device_ptr(d_seq)) || (cap && !is_device_ptr(d_out))) {
     set_error("god_sketch_noalloc: sequence and output must be device memory");
     return GOD_EINVAL;
@@ -1199,11 +1204,12 @@ extern "C" int god_sketch_noalloc(const uint8_t* d_seq, uint64_t len, const char
   unsigned long long host[2] = {0, 0};
   GOD_CK(cudaMemcpyAsync(host, scratch + n_tiles + 1, sizeof host, cudaMemcpyDeviceToHost, st));
   GOD_CK(cudaStreamSynchronize(st));
-  *n_out = host[0];
   if ((int)(host[1] & 0xFFFFFFFFu) == GOD_ETIMEOUT) {
+    // the total of a pass that gave up means nothing: *n_out stays 0
     set_error("god_sketch_noalloc: ordered-compaction look-back wait gave up");
     return GOD_ETIMEOUT;
   }
+  *n_out = host[0];
   return host[0] > cap ? GOD_ERANGE : GOD_OK;
 }
 

@@ -17,10 +17,14 @@ import pytest
 
 from paper_2211_08157_gb300 import synth
 
-pytestmark = pytest.mark.gpu
-
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "god.h")
 MAX_PATTERNED = int(re.search(r"#define GOD_NOALLOC_MAX_PATTERNED (\d+)ULL", open(HEADER).read()).group(1))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_2211_08157_gb300 as god
+    return god.load()
 
 
 @pytest.fixture(scope="module")
@@ -43,6 +47,7 @@ def _noalloc(L, torch, seq, pattern, shift, k, w, cap):
     return rc, n.value, keys, rec[:, 2], rec[:, 3]
 
 
+@pytest.mark.gpu
 def test_noalloc_matches_sketch_two_calls(env):
     god, L, torch = env
     rng = np.random.default_rng(77)
@@ -61,6 +66,7 @@ def test_noalloc_matches_sketch_two_calls(env):
         assert np.array_equal(z, want_z.astype(np.uint32))
 
 
+@pytest.mark.gpu
 def test_noalloc_reports_size_and_limits(env):
     god, L, torch = env
     rng = np.random.default_rng(78)
@@ -78,3 +84,22 @@ def test_noalloc_reports_size_and_limits(env):
     assert b"GOD_NOALLOC_MAX_PATTERNED" in L.god_last_error()
     # host memory is refused (it would need a device copy)
     assert L.god_sketch_noalloc(seq.ctypes.data, seq.size, b"1", 0, 15, 10, o.data_ptr(), 1, C.byref(cnt), None) == -1
+    # an output address that is 8- but not 16-byte aligned is refused before any launch
+    assert L.god_sketch_noalloc(d.data_ptr(), 16, b"1", 0, 15, 10, o.data_ptr() + 8, 1, C.byref(cnt), None) == -1
+    assert b"16-byte aligned" in L.god_last_error()
+
+
+def test_noalloc_limit_is_exact_on_host(lib):
+    """The largest promised patterned length is accepted in the tightest case
+    (k = 28, w = 255, the smallest sub-tile) and one more base is refused.
+    Fake, non-device pointers are used: a length that fits reaches the device
+    pointer check and is refused there, so nothing is launched."""
+    L = lib
+    cnt = C.c_uint64(7)
+    fake_seq, fake_out = 4096, 8192
+    rc = L.god_sketch_noalloc(fake_seq, MAX_PATTERNED, b"1", 0, 28, 255, fake_out, 1, C.byref(cnt), None)
+    assert rc == -1 and b"device memory" in L.god_last_error() and cnt.value == 0
+    rc = L.god_sketch_noalloc(fake_seq, MAX_PATTERNED + 1, b"1", 0, 28, 255, fake_out, 1, C.byref(cnt), None)
+    assert rc == -1 and b"GOD_NOALLOC_MAX_PATTERNED" in L.god_last_error()
+    rc = L.god_sketch_noalloc(fake_seq, 100, b"1", 0, 28, 255, fake_out + 8, 1, C.byref(cnt), None)
+    assert rc == -1 and b"16-byte aligned" in L.god_last_error()
