@@ -55,16 +55,19 @@ def sketch_ops_per_base(k: int) -> int:
     return 4 + 7 + 5 + 23 + (12 if k <= 15 else 24) + 2
 
 
-def recorded_traffic(kernel: str):
-    """Per-launch DRAM bytes from the committed ncu summary, if it was taken on
-    the current kernel source (source hash matches), else None."""
+def recorded_traffic(kernel: str, workload: str):
+    """Per-launch DRAM bytes (read + write) of `kernel` from the committed ncu
+    summary, if it was captured on this workload and on the current kernel
+    source (source hash matches), else None."""
     import hashlib
     path = os.path.join(ROOT, "profiles", f"{kernel}_traffic.json")
     src = os.path.join(ROOT, "paper_2211_08157_gb300", "csrc", "sketch.cu")
     try:
         d = json.load(open(path))
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()
-        return d["bytes_per_launch"] if d.get("source_sha256") == h else None
+        if d.get("source_sha256") != h or d.get("workload") != workload:
+            return None
+        return {"bytes_per_launch": d["bytes_per_launch"], "source": d.get("command", path)}
     except Exception:
         return None
 
@@ -173,28 +176,24 @@ def barrier(ws: int):
 
 
 # ----------------------------------------------------------------------------- CPU oracle
-def oracle_timing(wl, ref, reads, offs, sample_reads: int, threads: int):
-    """Oracle index build (single-threaded, whole reference) + oracle seeding of a
-    read sample over `threads` host threads; returns seconds for the full batch."""
+def oracle_step(idx_args, reads, offs, t: int, threads: int):
+    """One oracle step over the whole batch: index build of the whole reference
+    (single-threaded, as the oracle stands) + seeding of every read over
+    `threads` host threads. Returns (index s, seeding s, anchors)."""
     import oracle
-    oracle.build()
     t0 = time.perf_counter()
-    idx = oracle.Index(ref, wl.pattern, wl.k, wl.w, wl.max_occ)
+    idx = oracle.Index(*idx_args)
     t_index = time.perf_counter() - t0
-    n = offs.size - 1
-    m = min(sample_reads, n)
-    sub_offs = offs[: m + 1]
-    sub = reads[: int(sub_offs[-1])]
     t0 = time.perf_counter()
-    idx.seed(sub, sub_offs, wl.t, threads=threads)
+    a, _ = idx.seed(reads, offs, t, threads=threads)
     t_seed = time.perf_counter() - t0
     idx.close()
-    scale = n / m
-    return t_index, t_seed, scale, int(sub_offs[-1])
+    return t_index, t_seed, int(a.size)
 
 
 def run_reference(args, ws, rank):
-    """The oracle as the reference arm: host cores, bounded sample per step."""
+    """The oracle as the reference arm: the same step (index build + seeding of
+    the whole batch) on the host cores; rank 0 only."""
     if rank != 0:
         return
     wl, ref, reads, offs = make_workload(args.workload, args.n_reads, 0)
@@ -203,36 +202,33 @@ def run_reference(args, ws, rank):
     threads = os.cpu_count() or 1
     bases = float(offs[-1])
     n = offs.size - 1
-    m = min(args.ref_sample_reads, n)
-    t0 = time.perf_counter()
-    idx = oracle.Index(ref, wl.pattern, wl.k, wl.w, wl.max_occ)
-    t_index = time.perf_counter() - t0
-    sub_offs = offs[: m + 1]
-    sub = reads[: int(sub_offs[-1])]
+    idx_args = (ref, wl.pattern, wl.k, wl.w, wl.max_occ)
     for _ in range(args.warmup):
-        idx.seed(sub, sub_offs, wl.t, threads=threads)
-    times = []
-    n_anchor_sample = 0
+        oracle_step(idx_args, reads, offs, wl.t, threads)
+    steps = []
+    t_run0 = time.perf_counter()
     for _ in range(args.steps):
-        t0 = time.perf_counter()
-        a, _ = idx.seed(sub, sub_offs, wl.t, threads=threads)
-        times.append(time.perf_counter() - t0)
-        n_anchor_sample = a.size
-    t_seed = statistics.mean(times)
-    step_s = t_index + t_seed * n / m
+        steps.append(oracle_step(idx_args, reads, offs, wl.t, threads))
+    wall = time.perf_counter() - t_run0
+    step_s = statistics.mean(ti + ts for ti, ts, _ in steps)
+    t_index = statistics.mean(ti for ti, _, _ in steps)
+    t_seed = statistics.mean(ts for _, ts, _ in steps)
+    n_anchors = steps[-1][2]
     value = bases / step_s
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "read bases/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u8/u64 integer", "data": "synthetic",
         "config": {"workload": wl.name, "reads": n, "read_bases": int(bases), "ref_bases": int(ref.size),
-                   "pattern": wl.pattern, "k": wl.k, "w": wl.w, "max_occ": wl.max_occ, "pa_t": wl.t},
-        "anchors_per_s": n_anchor_sample * (n / m) / step_s,
+                   "pattern": wl.pattern, "k": wl.k, "w": wl.w, "max_occ": wl.max_occ, "pa_t": wl.t,
+                   "step": "index build + seeding of all reads"},
+        "anchors_per_s": n_anchors / step_s, "anchors_per_step": n_anchors,
         "cpu_baseline": {"value": value, "unit": "read bases/s", "cores": threads, "kind": "oracle",
-                         "sample": f"oracle index of the full {ref.size} bp reference (1 thread, {t_index:.1f} s) + "
-                                   f"oracle seeding of the first {m} of {n} reads per step over {threads} threads, "
-                                   f"scaled to the full batch"},
+                         "sample": f"the whole batch every step: oracle index of the {ref.size} bp reference on "
+                                   f"1 thread ({t_index:.2f} s) + oracle seeding of all {n} reads "
+                                   f"({int(bases)} bases) on {threads} threads ({t_seed:.2f} s)"},
         "e2e": {"value": value, "unit": "read bases/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "timed_wall_s": wall,
     }
     print(json.dumps(line), flush=True)
 
@@ -241,17 +237,7 @@ def run_reference(args, ws, rank):
 def serving_pool(ref, long_max=300, seed=5):
     """Request payloads: short-read batches (1k-50k x 150 bp) and long-read batches
     (HiFi-like and ONT-like, 10-long_max reads), each kind a third of the stream."""
-    rng = np.random.default_rng(seed)
-    pool = {"short": [], "hifi": [], "ont": []}
-    for i in range(8):
-        g = np.random.default_rng(seed * 100 + i)
-        pool["short"].append(synth.reads(ref, int(rng.integers(1000, 50001)), synth.SHORT, synth.ILLUMINA_INDEL, 0,
-                                         rng=g)[:2])
-        pool["hifi"].append(synth.reads(ref, int(rng.integers(10, long_max + 1)), synth.HIFI, synth.HIFI_ERR, 0,
-                                        rng=g)[:2])
-        pool["ont"].append(synth.reads(ref, int(rng.integers(10, long_max + 1)), synth.ONT, synth.ONT_ERR, 0,
-                                       rng=g)[:2])
-    return pool
+    return synth.serving_requests(ref, 8, long_max, seed)
 
 
 def seed_host(god, idx, reads, offs, via):
@@ -328,6 +314,75 @@ def run_serving(god, idx, pool, rate, duration, mode, slots=4, seed=11, saturate
             "batches": stats["batches"], "max_inflight_batches": stats["max_inflight_batches"]} if stats else {})}
 
 
+# ----------------------------------------------------------------------------- other workloads
+def time_events(stream, flush, fn, reps=3):
+    """Mean CUDA-event milliseconds of fn() on `stream`, L2 flushed before each."""
+    import torch
+    tt = []
+    for _ in range(reps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        stream.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        tt.append(e0.elapsed_time(e1))
+    return statistics.mean(tt)
+
+
+def workload_line(god, torch, dev, stream, flush, name, ref=None):
+    """Seeding throughput of one stated workload at its full size with a resident
+    index (inputs in HBM), hash against learned lookups, plus each index's build
+    time. Returns (line, reference array)."""
+    wl = synth.WORKLOADS[name]
+    t0 = time.perf_counter()
+    if ref is None:
+        ref = wl.make_reference()
+    reads, offs, _ = wl.make_reads(ref)
+    gen_s = time.perf_counter() - t0
+    bases = float(offs[-1])
+    d_ref = torch.from_numpy(ref).to(dev)
+    d_reads = torch.from_numpy(reads).to(dev)
+    d_offs = torch.from_numpy(offs.view(np.int64)).to(dev)
+    out = {"reads": int(offs.size - 1), "read_bases": int(bases), "ref_bases": int(ref.size), "pattern": wl.pattern,
+           "k": wl.k, "w": wl.w, "max_occ": wl.max_occ, "pa_t": wl.t, "input_generation_s": gen_s}
+    for nm, kd in (("hash", god.GOD_INDEX_HASH), ("learned", god.GOD_INDEX_LEARNED)):
+        prm = god.god_params_init(index_kind=kd, pa_t=wl.t)
+        holder = {}
+
+        def build():
+            if "idx" in holder:
+                holder.pop("idx").close()
+            holder["idx"] = god.god_build_index(d_ref, wl.pattern, wl.k, wl.w, wl.max_occ, params=prm,
+                                                stream=stream)
+
+        build_ms = time_events(stream, flush, build, reps=2)
+        idx = holder["idx"]
+        res = {}
+
+        def seed():
+            ptr, m = god.god_seed_device(idx, d_reads, d_offs, stream=stream)
+            res["m"] = m
+            god.god_free(ptr)
+
+        seed()
+        ms = time_events(stream, flush, seed)
+        info = idx.info
+        out[nm] = {"read_bases_per_s": bases / (ms / 1e3), "anchors_per_s": res["m"] / (ms / 1e3),
+                   "anchors": res["m"], "seed_ms": ms, "index_build_ms": build_ms}
+        if nm == "learned":
+            out[nm].update(rmi_mean_eps=info["rmi_mean_eps"], rmi_leaves=info["rmi_leaves"],
+                           rmi_fallback_key_frac=info["rmi_fallback_key_frac"])
+        idx.close()
+    out["learned_over_hash"] = out["learned"]["read_bases_per_s"] / out["hash"]["read_bases_per_s"]
+    del d_ref, d_reads, d_offs
+    torch.cuda.empty_cache()
+    return out, ref
+
+
 # ----------------------------------------------------------------------------- GPU arm
 def main():
     ap = argparse.ArgumentParser()
@@ -338,11 +393,11 @@ def main():
     ap.add_argument("--index", default="hash", choices=["hash", "learned"])
     ap.add_argument("--workload", default="short_100mbp_2m")
     ap.add_argument("--n-reads", type=int, default=None)
-    ap.add_argument("--cpu-sample-reads", type=int, default=200_000)
-    ap.add_argument("--ref-sample-reads", type=int, default=100_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the other index kind's seed-only line")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="skip the HiFi-like and human-scale ONT-like seeding lines")
     ap.add_argument("--serving-seconds", type=float, default=3.0, help="0 skips the serving measurement")
     ap.add_argument("--serving-rate", type=float, default=200.0)
     ap.add_argument("--serving-workload", default="ont_3100mbp_100k",
@@ -446,15 +501,21 @@ def main():
     tl, tms, tbytes, tunits = prof[tname] if tname in prof else prof_all[tname]
     per_launch_s = (tms / tl) / 1e3
     if tname == "sketch":
+        # algorithmic bytes: 1 B per patterned base read + 16 B per minimizer
+        # record written; the integer-issue view of the same launches beside it
+        bpl = tbytes / tl
+        achieved = bpl / per_launch_s / 1e9
         ops = sketch_ops_per_base(wl.k) * tunits / tl            # algorithmic int32 ops per launch
-        achieved = ops / per_launch_s / 1e12
-        roof = {"kernel": tname, "bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TOPS,
-                "unit": "Tops/s (int32, issue-limited)", "frac": achieved / ALU_PEAK_TOPS,
-                "traffic": recorded_traffic("sketch"), "peak_source": "derived from 152 SMs x 128 lanes x 2.07 GHz",
-                "ops_per_patterned_base": sketch_ops_per_base(wl.k), "ms_per_launch": tms / tl,
-                "hbm_view": {"achieved": (tbytes / tl) / per_launch_s / 1e9, "peak": hbm, "unit": "GB/s",
-                             "frac": (tbytes / tl) / per_launch_s / 1e9 / hbm, "peak_source": peak_src,
-                             "bytes_per_launch": tbytes / tl}}
+        tr = recorded_traffic("sketch", wl.name)
+        roof = {"kernel": tname, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": tr["bytes_per_launch"] if tr else None,
+                "traffic_source": tr["source"] if tr else "no capture on the current kernel source",
+                "peak_source": peak_src, "bytes_per_launch": bpl, "ms_per_launch": tms / tl,
+                "alu_view": {"achieved": ops / per_launch_s / 1e12, "peak": ALU_PEAK_TOPS,
+                             "unit": "Tops/s (int32, issue-limited)",
+                             "frac": ops / per_launch_s / 1e12 / ALU_PEAK_TOPS,
+                             "ops_per_patterned_base": sketch_ops_per_base(wl.k),
+                             "peak_source": "derived from 152 SMs x 128 lanes x 2.07 GHz"}}
     elif tbytes > 0:
         achieved = (tbytes / tl) / per_launch_s / 1e9
         roof = {"kernel": tname, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
@@ -551,10 +612,27 @@ def main():
     # ---- serving: request streams against a resident index; the server (the
     # index's learned lookups, continuous batching) against the plain path (one
     # god_seed call per request, hash lookups)
+    # ---- the other stated workloads at full size (rank 0): 200,000 HiFi-like
+    # reads on the 100 Mbp reference, 100,000 ONT-like reads on the 3.1 Gbp one
+    workloads = None
+    refs = {wl.name: ref}
+    if rank == 0 and not args.no_workloads:
+        workloads = {}
+        for wname in ("hifi_100mbp_200k", "ont_3100mbp_100k"):
+            r0 = None
+            wref_cfg = synth.WORKLOADS[wname].ref_config or synth.WORKLOADS[wname].config
+            for nm0, r in refs.items():
+                w0 = synth.WORKLOADS[nm0]
+                if (w0.ref_config or w0.config) == wref_cfg and w0.ref_len == synth.WORKLOADS[wname].ref_len:
+                    r0 = r
+            workloads[wname], refs[wname] = workload_line(god, torch, dev, stream, flush, wname, r0)
+
     serving = None
     if args.serving_seconds > 0 and rank == 0:
         swl = synth.WORKLOADS[args.serving_workload]
-        sref = ref if swl.name == wl.name else swl.make_reference()
+        sref = refs.get(swl.name)
+        if sref is None:
+            sref = swl.make_reference()
         pool = serving_pool(sref, long_max=args.serving_long_max)
         sp = god.god_params_init(index_kind=god.GOD_INDEX_LEARNED, pa_t=swl.t)
         t0 = time.perf_counter()
@@ -581,16 +659,18 @@ def main():
                                                                          saturate=True, via=0)}}
         sidx.close()
 
-    # ---- CPU oracle baseline (rank 0, N = 1 only)
+    # ---- CPU oracle baseline (rank 0, N = 1 only): one oracle step over the
+    # whole batch, as the oracle stands
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
         threads = os.cpu_count() or 1
-        t_index, t_seed, scale, sb = oracle_timing(wl, ref, reads, offs, args.cpu_sample_reads, threads)
-        full_s = t_index + t_seed * scale
-        cpu = {"value": bases / full_s, "unit": "read bases/s", "cores": threads, "kind": "oracle",
-               "sample": f"oracle index of the full {ref.size} bp reference on 1 thread ({t_index:.1f} s) + oracle "
-                         f"seeding of {min(args.cpu_sample_reads, n)} reads ({sb} bases) on {threads} threads "
-                         f"({t_seed:.1f} s), scaled to the {n}-read batch"}
+        t_index, t_seed, _ = oracle_step((ref, wl.pattern, wl.k, wl.w, wl.max_occ), reads, offs, wl.t, threads)
+        cpu = {"value": bases / (t_index + t_seed), "unit": "read bases/s", "cores": threads, "kind": "oracle",
+               "sample": f"the whole batch once: oracle index of the {ref.size} bp reference on 1 thread "
+                         f"({t_index:.2f} s) + oracle seeding of all {n} reads ({int(bases)} bases) on {threads} "
+                         f"threads ({t_seed:.2f} s)"}
 
     if rank == 0:
         line = {
@@ -608,7 +688,8 @@ def main():
             "gpu_launches": int(launches),
             "roofline": roof, "sketch_roofline": sketch_roof, "kernels": kernels,
             "kernels_note": f"per-step means over {prof_steps} extra steps with every launch timed by CUDA events",
-            "seed_only_resident_index": seed_only, "index_build_resident_reference": index_build, "serving": serving, "e2e": e2e, "cpu_baseline": cpu,
+            "seed_only_resident_index": seed_only, "index_build_resident_reference": index_build, "workloads": workloads, "serving": serving, "e2e": e2e,
+            "cpu_baseline": cpu,
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)

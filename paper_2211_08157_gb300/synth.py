@@ -303,3 +303,18 @@ WORKLOADS = {
     "ont_3100mbp_100k": Workload("ont_3100mbp_100k", 4, 3_100_000_000, REP_HUMAN, 100_000, ONT, ONT_ERR,
                                  "10", 15, 10, 1000),
 }
+
+
+def serving_requests(ref: np.ndarray, per_kind: int = 8, long_max: int = 2000, seed: int = 5):
+    """Request payloads of the serving workload: short-read batches (1k-50k x
+    150 bp, 0.1 % substitutions + 0.01 % 1-bp indels), HiFi-like and ONT-like
+    long-read batches (10-long_max reads, the length and error models above);
+    per_kind requests of each kind, as {kind: [(reads, offsets), ...]}."""
+    rng = np.random.default_rng(seed)
+    pool = {"short": [], "hifi": [], "ont": []}
+    for i in range(per_kind):
+        g = np.random.default_rng(seed * 100 + i)
+        pool["short"].append(reads(ref, int(rng.integers(1000, 50001)), SHORT, ILLUMINA_INDEL, 0, rng=g)[:2])
+        pool["hifi"].append(reads(ref, int(rng.integers(10, long_max + 1)), HIFI, HIFI_ERR, 0, rng=g)[:2])
+        pool["ont"].append(reads(ref, int(rng.integers(10, long_max + 1)), ONT, ONT_ERR, 0, rng=g)[:2])
+    return pool

@@ -27,8 +27,8 @@ def json_lines(text):
     return [json.loads(l) for l in text.splitlines() if l.startswith("{")]
 
 
-REF_ARGS = ["--impl", "reference", "--workload", "tiny_1mbp_short", "--steps", "1", "--warmup", "0",
-            "--ref-sample-reads", "2000"]
+REF_ARGS = ["--impl", "reference", "--workload", "tiny_1mbp_short", "--n-reads", "2000", "--steps", "1",
+            "--warmup", "0"]
 
 
 def test_reference_arm_single_rank():
@@ -43,7 +43,9 @@ def test_reference_arm_single_rank():
     assert L["e2e"]["value"] == L["value"] == L["cpu_baseline"]["value"]
     assert L["e2e"]["h2d_bytes_per_step"] == 0 and L["e2e"]["d2h_bytes_per_step"] == 0
     assert L["cpu_baseline"]["kind"] == "oracle" and L["cpu_baseline"]["cores"] >= 1
-    assert L["config"]["workload"] == "tiny_1mbp_short"
+    assert L["config"]["workload"] == "tiny_1mbp_short" and L["config"]["reads"] == 2000
+    # every step runs the whole batch: the timed steps fit in the measured wall time
+    assert L["ms_per_step"] * L["steps"] <= L["timed_wall_s"] * 1e3 * 1.01
 
 
 def test_reference_arm_two_ranks_rank0_only():

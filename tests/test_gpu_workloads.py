@@ -1,19 +1,29 @@
-"""Long-read workloads against the oracle.
+"""Long-read and serving workloads at their stated sizes, against the oracle.
 
-HiFi-like: the 100 Mbp reference (5 % repeats at 2 % divergence), 20,000
+HiFi-like: the 100 Mbp reference (5 % repeats at 2 % divergence), all 200,000
 reads with lognormal lengths (mean 15 kb, sd 4 kb, 2-30 kb) and 0.1 % errors
-(sub:ins:del 1:2:2), pattern 110, k = 19, w = 19, max_occ = 500: the
-pattern-alignment prefix is capped and every read takes the second seeding
-pass. 200 sampled reads are compared exactly with the oracle; hash and learned
-lookups must give identical lists.
+(sub:ins:del 1:2:2), pattern 110, k = 19, w = 19, max_occ = 500, in one
+batched device call. Every read's anchors and alignment index must equal the
+oracle's (all 200,000 reads); hash and learned lookups must give identical
+lists.
 
 ONT-like at human scale: the 3.1 Gbp reference (45 % of bases from repeat
 families of 300 bp-6 kb at 5-15 % divergence), pattern 10, k = 15, w = 10,
 max_occ = 1000. The whole filtered index (~0.28 G minimizers) must equal the
-oracle's; 4,000 reads (lognormal, mean 10 kb, 0.5-100 kb, 8 % errors 1:1:1)
-are seeded on the GPU and a seeded 10 % sample is compared exactly with the
-oracle.
+oracle's; all 100,000 reads (lognormal, mean 10 kb, 0.5-100 kb, 8 % errors
+1:1:1) are seeded in one device call with the hash and with the learned index
+(identical lists) and a seeded 10 % sample (10,000 reads) is compared exactly
+with the oracle.
+
+Serving at human scale: the learned index of the same 3.1 Gbp reference stays
+resident in a continuous-batching server; requests of the serving mix (short
+batches of 1k-50k reads, HiFi-like and ONT-like batches of 10-2,000 reads) are
+submitted together. Every request's anchors must equal those of the same reads
+seeded alone, and a sample of requests (one of each kind and more) must equal
+the oracle's.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -21,6 +31,8 @@ import oracle
 from paper_2211_08157_gb300 import synth
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+THREADS = os.cpu_count() or 8
 
 
 @pytest.fixture(scope="module")
@@ -33,16 +45,23 @@ def god():
     return g
 
 
+@pytest.fixture(scope="module")
+def human(god):
+    """The 3.1 Gbp reference and the oracle's index of it (built once)."""
+    wl = synth.WORKLOADS["ont_3100mbp_100k"]
+    ref = wl.make_reference()
+    o = oracle.Index(ref, wl.pattern, wl.k, wl.w, wl.max_occ)
+    yield wl, ref, o
+    o.close()
+
+
 def device_view(torch, ptr, m):
     class V:
         __cuda_array_interface__ = {"shape": (m, 4), "typestr": "<i4", "data": (ptr, False), "version": 2}
     return torch.as_tensor(V(), device="cuda")
 
 
-def seed_on_device(god, torch, idx, reads, offs, via):
-    d_reads = torch.from_numpy(reads).cuda()
-    d_offs = torch.from_numpy(offs.view(np.int64)).cuda()
-    n = offs.size - 1
+def seed_on_device(god, torch, idx, d_reads, d_offs, n, via):
     shifts = torch.zeros(n, dtype=torch.int32, device="cuda")
     ptr, m = god.god_seed_device(idx, d_reads, d_offs, via=via, shifts_out=shifts)
     return ptr, m, shifts.cpu().numpy().view(np.uint32)
@@ -55,8 +74,11 @@ def sample_rows(torch, A, sample):
     s = torch.from_numpy(sample.astype(np.int32)).cuda()
     lo = torch.searchsorted(rid, s, side="left")
     hi = torch.searchsorted(rid, s, side="right")
-    parts = [A[int(l):int(h)] for l, h in zip(lo.tolist(), hi.tolist())]
-    got = torch.cat(parts).cpu().numpy().view(np.uint32).copy() if parts else np.zeros((0, 4), np.uint32)
+    keep = torch.zeros(A.shape[0] + 1, dtype=torch.int32, device="cuda")
+    keep.index_add_(0, lo, torch.ones_like(lo, dtype=torch.int32))
+    keep.index_add_(0, hi, -torch.ones_like(hi, dtype=torch.int32))
+    mask = torch.cumsum(keep, 0)[:-1] > 0
+    got = A[mask].cpu().numpy().view(np.uint32).copy()
     got[:, 0] = np.repeat(np.arange(sample.size, dtype=np.uint32), (hi - lo).cpu().numpy())
     return got
 
@@ -68,43 +90,43 @@ def subset(reads, offs, sample):
     return np.concatenate([reads[int(offs[i]):int(offs[i + 1])] for i in sample]), so
 
 
-def test_hifi_workload(god):
+def test_hifi_workload_full(god):
     import torch
     wl = synth.WORKLOADS["hifi_100mbp_200k"]
     ref = wl.make_reference()
-    reads, offs, _ = wl.make_reads(ref, n=20_000)
+    reads, offs, _ = wl.make_reads(ref)
+    n = offs.size - 1
+    assert n == 200_000
     d_ref = torch.from_numpy(ref).cuda()
+    d_reads = torch.from_numpy(reads).cuda()
+    d_offs = torch.from_numpy(offs.view(np.int64)).cuda()
     res = {}
     for via, kind in ((0, god.GOD_INDEX_HASH), (1, god.GOD_INDEX_LEARNED)):
         idx = god.god_build_index(d_ref, wl.pattern, wl.k, wl.w, wl.max_occ,
                                   params=god.god_params_init(index_kind=kind, pa_t=wl.t))
-        ptr, m, shifts = seed_on_device(god, torch, idx, reads, offs, via)
+        ptr, m, shifts = seed_on_device(god, torch, idx, d_reads, d_offs, n, via)
         A = device_view(torch, ptr, m)
-        res[via] = (A.clone(), shifts)
+        res[via] = (A.cpu().numpy().view(np.uint32).copy(), shifts)
         god.god_free(ptr)
         idx.close()
-    A0, s0 = res[0]
-    A1, s1 = res[1]
-    assert torch.equal(A0, A1) and np.array_equal(s0, s1)
-    assert A0.shape[0] > 1_000_000
-    rng = np.random.default_rng(303)
-    sample = np.sort(rng.choice(offs.size - 1, 200, replace=False))
-    sub, so = subset(reads, offs, sample)
-    want, wshift = oracle.Index(ref, wl.pattern, wl.k, wl.w, wl.max_occ).seed(sub, so, wl.t, threads=8)
-    assert np.array_equal(s0[sample], wshift)
-    got = sample_rows(torch, A0, sample)
-    assert np.array_equal(got.reshape(-1), want.view(np.uint32))
+    a0, s0 = res[0]
+    a1, s1 = res[1]
+    assert np.array_equal(a0, a1) and np.array_equal(s0, s1)
+    assert a0.shape[0] > 10_000_000
+    want, wshift = oracle.Index(ref, wl.pattern, wl.k, wl.w, wl.max_occ).seed(reads, offs, wl.t, threads=THREADS)
+    assert np.array_equal(s0, wshift)
+    assert want.size == a0.shape[0]
+    assert np.array_equal(a0.reshape(-1), want.view(np.uint32))
 
 
-def test_ont_human_scale_index_and_sample(god):
+def test_ont_human_scale_index_and_sample(god, human):
     import torch
-    wl = synth.WORKLOADS["ont_3100mbp_100k"]
-    ref = wl.make_reference()
+    wl, ref, o = human
     d_ref = torch.from_numpy(ref).cuda()
     idx = god.god_build_index(d_ref, wl.pattern, wl.k, wl.w, wl.max_occ,
-                              params=god.god_params_init(pa_t=wl.t))
+                              params=god.god_params_init(index_kind=god.GOD_INDEX_LEARNED, pa_t=wl.t))
+    del d_ref
     info = idx.info
-    o = oracle.Index(ref, wl.pattern, wl.k, wl.w, wl.max_occ)
     assert info["n_minimizers"] == o.sizes()[0] and info["n_minimizers"] > 250_000_000
     gk, gs, ge = god.god_index_export(idx)
     ok, os_, oe = o.dump()
@@ -112,15 +134,59 @@ def test_ont_human_scale_index_and_sample(god):
     assert np.array_equal(gs, os_)
     assert np.array_equal(ge, oe)
     del gk, gs, ge, ok, os_, oe
-    reads, offs, _ = wl.make_reads(ref, n=4000)
-    ptr, m, shifts = seed_on_device(god, torch, idx, reads, offs, 0)
-    A = device_view(torch, ptr, m)
+    reads, offs, _ = wl.make_reads(ref)
+    n = offs.size - 1
+    assert n == 100_000
+    d_reads = torch.from_numpy(reads).cuda()
+    d_offs = torch.from_numpy(offs.view(np.int64)).cuda()
+    ptr0, m0, shifts0 = seed_on_device(god, torch, idx, d_reads, d_offs, n, 0)
+    ptr1, m1, shifts1 = seed_on_device(god, torch, idx, d_reads, d_offs, n, 1)
+    A0 = device_view(torch, ptr0, m0)
+    A1 = device_view(torch, ptr1, m1)
+    assert m0 == m1 and torch.equal(A0, A1) and np.array_equal(shifts0, shifts1)
+    god.god_free(ptr1)
     rng = np.random.default_rng(404)
-    sample = np.sort(rng.choice(offs.size - 1, 400, replace=False))
+    sample = np.sort(rng.choice(n, n // 10, replace=False))
     sub, so = subset(reads, offs, sample)
-    want, wshift = o.seed(sub, so, wl.t, threads=8)
-    assert np.array_equal(shifts[sample], wshift)
-    got = sample_rows(torch, A, sample)
-    god.god_free(ptr)
+    want, wshift = o.seed(sub, so, wl.t, threads=THREADS)
+    assert np.array_equal(shifts0[sample], wshift)
+    got = sample_rows(torch, A0, sample)
+    god.god_free(ptr0)
+    assert got.shape[0] == want.size
     assert np.array_equal(got.reshape(-1), want.view(np.uint32))
+    idx.close()
+
+
+def test_serving_human_scale_learned_index(god, human):
+    import torch
+    wl, ref, o = human
+    idx = god.god_build_index(torch.from_numpy(ref).cuda(), wl.pattern, wl.k, wl.w, wl.max_occ,
+                              params=god.god_params_init(index_kind=god.GOD_INDEX_LEARNED, pa_t=wl.t))
+    pool = synth.serving_requests(ref, per_kind=4, long_max=2000, seed=21)
+    rng = np.random.default_rng(22)
+    reqs = []
+    for kind in ("short", "hifi", "ont"):
+        reqs += [(kind, r, off) for r, off in pool[kind]]
+    order = rng.permutation(len(reqs))
+    reqs = [reqs[i] for i in order]
+    srv = god.GodServer(idx, slots=4)
+    ids = [srv.submit(r, off) for _, r, off in reqs]
+    got = [srv.wait(i) for i in ids]
+    st = srv.stats()
+    srv.close()
+    assert st["submitted"] == st["completed"] == len(reqs)
+    for (_, r, off), g in zip(reqs, got):
+        alone = god.god_seed(idx, r, off)
+        assert alone.size == g.size and np.array_equal(alone, g)
+    # oracle parity: the first request of each kind and two more
+    picked, seen = [], set()
+    for q, (kind, _, _) in enumerate(reqs):
+        if kind not in seen:
+            seen.add(kind)
+            picked.append(q)
+    picked += [q for q in range(len(reqs)) if q not in picked][:2]
+    for q in picked:
+        _, r, off = reqs[q]
+        want, _ = o.seed(r, off, wl.t, threads=THREADS)
+        assert np.array_equal(got[q], want), f"request {q} ({reqs[q][0]}) differs from the oracle"
     idx.close()
