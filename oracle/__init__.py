@@ -7,7 +7,8 @@ imports this module, and this module imports nothing from the product package.
 Every function mirrors one step of the method (paper sections in the C++ file):
 sparsification (Sec. 3, 3.2), the Wang integer hash (Sec. 3.6.1), (w,k)-minimizers
 (Sec. 3.1), the filtered seed index (Sec. 3.1, 3.2), pattern alignment (Sec. 3.2),
-compressed seeding to sorted anchors (Sec. 3.3), and the learned-index reference.
+compressed seeding to sorted anchors (Sec. 3.3), location voting with the rescue
+location (Sec. 3.4, Sec. 3.6.3), and the learned-index reference.
 """
 from __future__ import annotations
 
@@ -25,6 +26,8 @@ _lock = threading.Lock()
 _lib = None
 
 ANCHOR_DTYPE = np.dtype([("read_id", "<u4"), ("read_pos", "<u4"), ("ref_pos", "<u4"), ("strand", "<u4")])
+VOTE_DTYPE = np.dtype([("read_id", "<u4"), ("votes", "<u4"), ("strand", "<u4"), ("rescue", "<u4"), ("loc", "<i8"),
+                       ("ref_lo", "<u4"), ("ref_hi", "<u4"), ("read_lo", "<u4"), ("read_hi", "<u4")])
 
 
 def build(force: bool = False) -> str:
@@ -65,6 +68,8 @@ def lib():
             L.orc_pattern_align.argtypes = [p, p, u64, u32, p]
             L.orc_seed.restype = C.POINTER(C.c_uint32)
             L.orc_seed.argtypes = [p, p, p, u32, u32, i32, C.POINTER(u64), p]
+            L.orc_vote.restype = i32
+            L.orc_vote.argtypes = [p, u64, p, u32, u32, u32, u32, p, p]
             L.orc_free.restype = None
             L.orc_free.argtypes = [p]
             L.orc_root_loss_grad_f64.restype = C.c_double
@@ -181,6 +186,23 @@ class Index:
         arr = np.ctypeslib.as_array(buf, shape=(max(m, 1) * 4,))[: m * 4].copy()
         lib().orc_free(C.cast(buf, C.c_void_p))
         return arr.view(ANCHOR_DTYPE), shifts[:n]
+
+
+def vote(anchors, offsets, D: int, V: int, max_out: int):
+    """Location voting (Sec. 3.4, Sec. 3.6.3) over an anchor list grouped by
+    ascending read id. Returns (records of every read in read order, as
+    VOTE_DTYPE, and the per-read record counts)."""
+    a = np.ascontiguousarray(np.asarray(anchors).view(np.uint32).reshape(-1, 4))
+    offs = np.ascontiguousarray(offsets, dtype=np.uint64)
+    n = offs.size - 1
+    out = np.zeros(max(n * max_out, 1), VOTE_DTYPE)
+    counts = np.zeros(max(n, 1), np.uint32)
+    rc = lib().orc_vote(_ptr(a), a.shape[0], _ptr(offs), n, D, V, max_out, _ptr(out), _ptr(counts))
+    if rc != 0:
+        raise ValueError("anchors must be grouped by ascending read id < number of reads")
+    counts = counts[:n]
+    keep = (np.arange(max_out)[None, :] < counts[:, None]).reshape(-1)
+    return out[: n * max_out][keep], counts
 
 
 def root_loss_grad_f64(theta: np.ndarray, H: int, x: np.ndarray, y: np.ndarray):

@@ -15,6 +15,8 @@
 //   * the compressed seed index: sort, group by key, high-occurrence filter
 //     (Sec. 3.1 step 3, Sec. 3.2);
 //   * pattern alignment (Sec. 3.2) and compressed seeding to anchors (Sec. 3.3);
+//   * location voting on each read's anchors, with the rescue location
+//     (Sec. 3.4, Fig. 8, Sec. 3.6.3);
 //   * the learned-index (RMI) reference: MLP root forward/backward, leaf least
 //     squares and per-leaf error bounds in the same FP32 operation order the GPU
 //     lookup uses.
@@ -297,6 +299,85 @@ void seed_range(const Index* idx, const uint8_t* reads, const uint64_t* offsets,
     if (shifts) shifts[r] = a;
     seed_read(idx, r, q, len, a, out);
   }
+}
+
+// ---------------------------------------------------------------- location voting
+// Sec. 3.4 (steps 1-5, Fig. 8) and Sec. 3.6.3 (rescue) for one read's anchors.
+// Readings where the paper is silent:
+//   * step 1 rebases every anchor to one signed location: v = ref_pos - read_pos
+//     on the forward strand; on the reverse strand the read position is taken
+//     from the read's other end, v = ref_pos - (len - 1 - read_pos). Every
+//     anchor is one vote (no de-duplication: Fig. 8A counts 12 votes at one
+//     location).
+//   * the two strands vote separately; the single sorted list of step 2 is
+//     ordered by (strand, v).
+//   * step 3: a group starts at the first location v0 of what is left and takes
+//     every location of the same strand with v - v0 <= D; the next group starts
+//     at the first location beyond that (steps 4 and 5 "repeat").
+//   * a group with at least V votes is a winner: (strand, v0, votes) for short
+//     reads (step 4), and the reference and read stretches its anchors cover,
+//     [min ref_pos, max ref_pos] and [min read_pos, max read_pos], for long
+//     reads (step 5; Fig. 8B's three stretches with 7, 8 and 3 votes at D = 100,
+//     V = 3). Every record carries both.
+//   * winners are ordered by votes, most first, equal votes in (strand, v0)
+//     order, and the list is cut to max_out entries (the user-defined limit).
+//   * rescue (Sec. 3.6.3): the group with the most votes (the first in
+//     (strand, v0) order on ties), whatever its count, is reported alone,
+//     flagged, when no group reaches V.
+struct VoteRec {
+  uint32_t read_id, votes, strand, rescue;
+  int64_t loc;
+  uint32_t ref_lo, ref_hi, read_lo, read_hi;
+};
+
+struct Located {
+  uint32_t strand;
+  int64_t v;
+  uint32_t ref_pos, read_pos;
+};
+
+void vote_read(uint32_t read_id, const Anchor* a, size_t n, uint64_t len, uint32_t D, uint32_t V,
+               uint32_t max_out, std::vector<VoteRec>& out) {
+  std::vector<Located> loc(n);
+  for (size_t i = 0; i < n; ++i) {
+    const int64_t ref = a[i].ref_pos, rp = a[i].read_pos;
+    const int64_t v = a[i].strand == 0 ? ref - rp : ref - ((int64_t)len - 1 - rp);
+    loc[i] = Located{a[i].strand, v, a[i].ref_pos, a[i].read_pos};
+  }
+  std::sort(loc.begin(), loc.end(), [](const Located& x, const Located& y) {
+    if (x.strand != y.strand) return x.strand < y.strand;
+    return x.v < y.v;
+  });
+  std::vector<VoteRec> groups;
+  size_t i = 0;
+  while (i < n) {
+    VoteRec g{read_id, 0, loc[i].strand, 0, loc[i].v, loc[i].ref_pos, loc[i].ref_pos, loc[i].read_pos,
+              loc[i].read_pos};
+    size_t j = i;
+    while (j < n && loc[j].strand == g.strand && loc[j].v - g.loc <= (int64_t)D) {
+      g.votes++;
+      g.ref_lo = std::min(g.ref_lo, loc[j].ref_pos);
+      g.ref_hi = std::max(g.ref_hi, loc[j].ref_pos);
+      g.read_lo = std::min(g.read_lo, loc[j].read_pos);
+      g.read_hi = std::max(g.read_hi, loc[j].read_pos);
+      ++j;
+    }
+    groups.push_back(g);
+    i = j;
+  }
+  std::vector<VoteRec> win;
+  for (const VoteRec& g : groups)
+    if (g.votes >= V) win.push_back(g);
+  std::stable_sort(win.begin(), win.end(), [](const VoteRec& x, const VoteRec& y) { return x.votes > y.votes; });
+  if (win.size() > max_out) win.resize(max_out);
+  if (win.empty() && !groups.empty()) {
+    VoteRec best = groups[0];
+    for (const VoteRec& g : groups)
+      if (g.votes > best.votes) best = g;
+    best.rescue = 1;
+    win.push_back(best);
+  }
+  out.insert(out.end(), win.begin(), win.end());
 }
 
 // ---------------------------------------------------------------- RMI reference
@@ -591,6 +672,33 @@ void orc_rmi_fit_leaves(const float* theta, int H, const uint64_t* keys, uint64_
     const uint64_t e = (uint64_t)err;
     if (e > eps[l]) eps[l] = (uint32_t)std::min<uint64_t>(e, 0xFFFFFFFFu);
   }
+}
+
+
+// Location voting over an anchor list grouped by ascending read_id (4 x u32
+// records, as orc_seed returns them); offsets = the reads' CSR byte offsets
+// (n_reads + 1), for the read lengths. Read r's records go to
+// out[r * max_out ...] (10 x u32 each: read_id, votes, strand, rescue, loc as
+// int64 little-endian, ref_lo, ref_hi, read_lo, read_hi), their number to
+// counts[r]. Returns 0, or -1 when the list is not grouped by read or names a
+// read >= n_reads.
+int orc_vote(const uint32_t* anchors, uint64_t n_anchors, const uint64_t* offsets, uint32_t n_reads,
+             uint32_t D, uint32_t V, uint32_t max_out, uint32_t* out, uint32_t* counts) {
+  const Anchor* a = reinterpret_cast<const Anchor*>(anchors);
+  for (uint32_t r = 0; r < n_reads; ++r) counts[r] = 0;
+  uint64_t i = 0;
+  while (i < n_anchors) {
+    const uint32_t r = a[i].read_id;
+    if (r >= n_reads || (i > 0 && r < a[i - 1].read_id)) return -1;
+    uint64_t j = i;
+    while (j < n_anchors && a[j].read_id == r) ++j;
+    std::vector<VoteRec> res;
+    vote_read(r, a + i, j - i, offsets[r + 1] - offsets[r], D, V, max_out, res);
+    counts[r] = (uint32_t)res.size();
+    std::memcpy(out + (uint64_t)r * max_out * 10, res.data(), res.size() * sizeof(VoteRec));
+    i = j;
+  }
+  return 0;
 }
 
 }  // extern "C"
