@@ -221,6 +221,51 @@ typedef struct {
 int god_sketch_noalloc(const uint8_t *d_seq, uint64_t len, const char *pattern, uint32_t shift, int k,
                        int w, god_minimizer *d_out, uint64_t cap, uint64_t *n_out, void *stream);
 
+/* ----------------------------------------------------------------- location voting
+ * god_vote: location voting on each read's anchors (Sec. 3.4 steps 1-5,
+ * Fig. 8) with the rescue location (Sec. 3.6.3).
+ *   1. every anchor is one vote at a signed location v = ref_pos - read_pos
+ *      (strand 0) or v = ref_pos - (len - 1 - read_pos) (strand 1: the read
+ *      position counted from the read's other end; for an error-free reverse
+ *      read this is its reference start minus (k-mer span - 1));
+ *   2. the votes of a read are ordered by (strand, v);
+ *   3. a group starts at the first vote left and takes every vote of the same
+ *      strand with v - v0 <= D; the next group starts at the first vote beyond;
+ *   4/5. groups with at least V votes are the read's winners, most votes first
+ *      (equal votes in (strand, v0) order), at most max_out of them. Each
+ *      record holds the location v0 and its votes (short reads, step 4) and
+ *      the reference and read stretches its anchors cover, [ref_lo, ref_hi]
+ *      and [read_lo, read_hi] (long reads, step 5);
+ *   rescue: when no group reaches V, the group with the most votes (the first
+ *      on ties) is reported alone with rescue = 1; a read without anchors
+ *      reports nothing.
+ *   anchors  host or device, n_anchors records grouped by ascending read_id
+ *            (any order inside a read), e.g. a god_seed result; 4-byte aligned.
+ *   offsets  host or device, n_reads + 1 CSR byte offsets of the reads (the
+ *            read lengths), as given to god_seed.
+ *   out      host or device, n_reads * max_out records: read r's are
+ *            out[r * max_out + j], j < counts[r]; 8-byte aligned.
+ *   counts   host or device (the same kind as out), n_reads entries.
+ * Errors: GOD_EINVAL for NULL arrays, V < 1, max_out outside 1..32, a
+ * misaligned device array, anchors not grouped by ascending read id or naming
+ * a read >= n_reads (found on the device before any result is written), or a
+ * read with 2^28 anchors or more; GOD_ENOMEM, GOD_ECUDA. The stream is
+ * synchronised before the call returns. */
+typedef struct {
+  uint32_t read_id, votes, strand, rescue;
+  int64_t loc;                          /* v0 */
+  uint32_t ref_lo, ref_hi, read_lo, read_hi;
+} god_vote_rec;                             /* 40 bytes */
+
+typedef struct {
+  uint32_t D;          /* maximum distance from a group's first location */
+  uint32_t V;          /* votes a winner needs (>= 1) */
+  uint32_t max_out;    /* winners kept per read, 1..32 */
+} god_vote_params;
+
+int god_vote(const god_anchor *anchors, uint64_t n_anchors, const uint64_t *offsets, uint32_t n_reads,
+             const god_vote_params *params, god_vote_rec *out, uint32_t *counts, void *stream);
+
 /* ----------------------------------------------------------------- learned index
  * Gradient of the root MLP's mean squared error (1 -> H -> 1, ReLU; parameter
  * layout W1[H], b1[H], W2[H], b2) over samples (x[i], y[i]), computed by the

@@ -14,9 +14,12 @@ import weakref
 import numpy as np
 
 from . import _lib
-from ._lib import GodError, IndexInfo, Params, SeedOpts, ServerConfig, ServerStats, build, check, load
+from ._lib import (GodError, IndexInfo, Params, SeedOpts, ServerConfig, ServerStats, VoteParams, build, check,
+                   load)
 
 ANCHOR_DTYPE = np.dtype([("read_id", "<u4"), ("read_pos", "<u4"), ("ref_pos", "<u4"), ("strand", "<u4")])
+VOTE_DTYPE = np.dtype([("read_id", "<u4"), ("votes", "<u4"), ("strand", "<u4"), ("rescue", "<u4"), ("loc", "<i8"),
+                       ("ref_lo", "<u4"), ("ref_hi", "<u4"), ("read_lo", "<u4"), ("read_hi", "<u4")])
 
 GOD_INDEX_HASH, GOD_INDEX_LEARNED = 0, 1
 GOD_ROOT_MLP, GOD_ROOT_UNTRAINED, GOD_ROOT_LINEAR = 0, 1, 2
@@ -205,6 +208,38 @@ def god_sketch(seq, pattern: str, shift: int, k: int, w: int, stream=None):
     check(L.god_sketch(_ptr(seq), n, pattern.encode(), shift, k, w, _ptr(keys), _ptr(pos), _ptr(z), m,
                        C.byref(cnt), _stream_ptr(stream)))
     return keys[:m], pos[:m], z[:m]
+
+
+def _numel(x):
+    return x.size if isinstance(x, np.ndarray) else x.numel()
+
+
+def god_vote(anchors, offsets, D: int, V: int, max_out: int, out=None, counts=None, stream=None):
+    """Location voting (god_vote) over an anchor list grouped by read id.
+
+    Host inputs without `out`: returns (records of every read in read order as
+    VOTE_DTYPE, per-read counts). With `out` (n_reads * max_out records: a
+    numpy VOTE_DTYPE array or a device tensor of 40-byte rows) and `counts`,
+    fills them in place and returns None. `n_anchors` comes from `anchors`
+    (structured numpy array, (m, 4) array or tensor); a (ptr, m) pair of a
+    device anchor list is accepted too."""
+    if isinstance(anchors, tuple):
+        a_ptr, m = anchors
+    else:
+        a_ptr = _ptr(anchors)
+        m = _numel(anchors) if (isinstance(anchors, np.ndarray) and anchors.dtype.names) else _numel(anchors) // 4
+    n = _numel(offsets) - 1
+    prm = VoteParams(D, V, max_out)
+    L = load()
+    if out is not None:
+        check(L.god_vote(a_ptr, m, _ptr(offsets), n, C.byref(prm), _ptr(out), _ptr(counts), _stream_ptr(stream)))
+        return None
+    rec = np.zeros(max(n * max_out, 1), VOTE_DTYPE)
+    cnt = np.zeros(max(n, 1), np.uint32)
+    check(L.god_vote(a_ptr, m, _ptr(offsets), n, C.byref(prm), _ptr(rec), _ptr(cnt), _stream_ptr(stream)))
+    cnt = cnt[:n]
+    keep = (np.arange(max_out)[None, :] < cnt[:, None]).reshape(-1)
+    return rec[: n * max_out][keep], cnt
 
 
 def god_rmi_root_grad(theta, H: int, x, y):

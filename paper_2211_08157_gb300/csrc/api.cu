@@ -670,6 +670,51 @@ int god_seed(const god_index* idx, const uint8_t* reads, const uint64_t* offsets
   return GOD_OK;
 }
 
+int god_vote(const god_anchor* anchors, uint64_t n_anchors, const uint64_t* offsets, uint32_t n_reads,
+             const god_vote_params* params, god_vote_rec* out, uint32_t* counts, void* stream) {
+  if (!params || (n_reads && (!offsets || !out || !counts)) || (n_anchors && !anchors)) {
+    set_error("god_vote: null argument");
+    return GOD_EINVAL;
+  }
+  if (params->V < 1 || params->max_out < 1 || params->max_out > 32) {
+    set_error("god_vote: V must be >= 1 and max_out in 1..32");
+    return GOD_EINVAL;
+  }
+  if (n_reads == 0) return GOD_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool dev_out = is_device_ptr(out);
+  if (dev_out != is_device_ptr(counts)) {
+    set_error("god_vote: out and counts must both be device or both host memory");
+    return GOD_EINVAL;
+  }
+  if ((dev_out && ((reinterpret_cast<uintptr_t>(out) & 7u) || (reinterpret_cast<uintptr_t>(counts) & 3u))) ||
+      (is_device_ptr(anchors) && (reinterpret_cast<uintptr_t>(anchors) & 3u)) ||
+      (is_device_ptr(offsets) && (reinterpret_cast<uintptr_t>(offsets) & 7u))) {
+    set_error("god_vote: misaligned device array");
+    return GOD_EINVAL;
+  }
+  DBuf<uint8_t> hold_a, hold_o;
+  const void* da = nullptr;
+  const void* doff = nullptr;
+  GOD_TRY(to_device(anchors, n_anchors * sizeof(god_anchor), hold_a, &da, st));
+  GOD_TRY(to_device(offsets, ((uint64_t)n_reads + 1) * 8, hold_o, &doff, st));
+  if (dev_out) {
+    GOD_TRY(vote_device((const god_anchor*)da, n_anchors, (const uint64_t*)doff, n_reads, *params, out, counts, st));
+    GOD_CK(cudaStreamSynchronize(st));
+    return GOD_OK;
+  }
+  DBuf<god_vote_rec> dv;
+  DBuf<uint32_t> dc;
+  GOD_TRY(dv.alloc((uint64_t)n_reads * params->max_out, st));
+  GOD_TRY(dc.alloc(n_reads, st));
+  GOD_TRY(vote_device((const god_anchor*)da, n_anchors, (const uint64_t*)doff, n_reads, *params, dv.p, dc.p, st));
+  GOD_CK(cudaMemcpyAsync(counts, dc.p, (uint64_t)n_reads * 4, cudaMemcpyDeviceToHost, st));
+  GOD_CK(cudaMemcpyAsync(out, dv.p, (uint64_t)n_reads * params->max_out * sizeof(god_vote_rec), cudaMemcpyDeviceToHost,
+                         st));
+  GOD_CK(cudaStreamSynchronize(st));
+  return GOD_OK;
+}
+
 int god_rmi_root_grad(const float* theta, int H, const float* x, const float* y, uint64_t n, float* grad, float* loss) {
   if (!theta || !grad || !loss || (n && (!x || !y)) || H != kRootHidden) return GOD_EINVAL;
   const int np = 3 * H + 1;

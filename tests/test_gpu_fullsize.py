@@ -8,6 +8,7 @@ indels, both strands), pattern 10, k = 21, w = 11, max_occ = 500, t = 32.
 * All 2,000,000 reads are seeded in one batched device call (hash and learned
   index) and the whole anchor list and every read's alignment index must equal
   what the oracle computes for all 2,000,000 reads (integer results: exact).
+* Location voting of all 2,000,000 reads on the GPU equals the oracle's.
 * Properties that hold at any size: the anchor list is sorted by
   (read_id, ref_pos, read_pos, strand) with no duplicates, and both index
   paths return identical lists.
@@ -72,3 +73,8 @@ def test_fullsize_seeding_full_parity(env):
     assert np.array_equal(s0, wshift)
     assert want.size == a0.shape[0]
     assert np.array_equal(a0.reshape(-1), want.view(np.uint32))
+    # location voting over the whole anchor list (Sec. 3.4 step 4, short reads)
+    d_a = torch.from_numpy(a0.view(np.int32)).cuda()
+    gv, gc = god.god_vote(d_a, offs, 50, 2, 4)
+    wv, wc = oracle.vote(want, offs, 50, 2, 4)
+    assert np.array_equal(gc, wc) and np.array_equal(gv, wv)

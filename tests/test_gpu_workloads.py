@@ -13,7 +13,8 @@ max_occ = 1000. The whole filtered index (~0.28 G minimizers) must equal the
 oracle's; all 100,000 reads (lognormal, mean 10 kb, 0.5-100 kb, 8 % errors
 1:1:1) are seeded in one device call with the hash and with the learned index
 (identical lists) and a seeded 10 % sample (10,000 reads) is compared exactly
-with the oracle.
+with the oracle. Location voting runs on every read of both long-read batches
+and must equal the oracle's (all HiFi-like reads, the ONT-like sample).
 
 Serving at human scale: the learned index of the same 3.1 Gbp reference stays
 resident in a continuous-batching server; requests of the serving mix (short
@@ -117,6 +118,10 @@ def test_hifi_workload_full(god):
     assert np.array_equal(s0, wshift)
     assert want.size == a0.shape[0]
     assert np.array_equal(a0.reshape(-1), want.view(np.uint32))
+    # location voting of every read (Sec. 3.4 step 5, long reads)
+    gv, gc = god.god_vote(a0, offs, 100, 3, 8)
+    wv, wc = oracle.vote(want, offs, 100, 3, 8)
+    assert np.array_equal(gc, wc) and np.array_equal(gv, wv)
 
 
 def test_ont_human_scale_index_and_sample(god, human):
@@ -151,9 +156,23 @@ def test_ont_human_scale_index_and_sample(god, human):
     want, wshift = o.seed(sub, so, wl.t, threads=THREADS)
     assert np.array_equal(shifts0[sample], wshift)
     got = sample_rows(torch, A0, sample)
-    god.god_free(ptr0)
     assert got.shape[0] == want.size
     assert np.array_equal(got.reshape(-1), want.view(np.uint32))
+    # location voting of all 100,000 reads on the device; the sample's records
+    # must equal the oracle's voting over the oracle's anchors
+    D, V, max_out = 100, 3, 8
+    d_out = torch.zeros((n * max_out, 10), dtype=torch.int32, device="cuda")
+    d_cnt = torch.zeros(n, dtype=torch.int32, device="cuda")
+    god.god_vote((ptr0, m0), d_offs, D, V, max_out, out=d_out, counts=d_cnt)
+    god.god_free(ptr0)
+    cnt = d_cnt.cpu().numpy().view(np.uint32)
+    rec = d_out.cpu().numpy().view(oracle.VOTE_DTYPE).reshape(n, max_out)
+    wv, wc = oracle.vote(want, so, D, V, max_out)
+    assert np.array_equal(cnt[sample], wc)
+    keep = np.arange(max_out)[None, :] < wc[:, None]
+    gv = rec[sample][keep].copy()
+    gv["read_id"] = np.repeat(np.arange(sample.size, dtype=np.uint32), wc)
+    assert np.array_equal(gv, wv)
     idx.close()
 
 
