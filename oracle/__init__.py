@@ -68,6 +68,8 @@ def lib():
             L.orc_pattern_align.argtypes = [p, p, u64, u32, p]
             L.orc_seed.restype = C.POINTER(C.c_uint32)
             L.orc_seed.argtypes = [p, p, p, u32, u32, i32, C.POINTER(u64), p]
+            L.orc_seed_segments.restype = C.POINTER(C.c_uint32)
+            L.orc_seed_segments.argtypes = [p, p, p, u32, u32, i32, u64, C.POINTER(u64), p]
             L.orc_vote.restype = i32
             L.orc_vote.argtypes = [p, u64, p, u32, u32, u32, u32, p, p]
             L.orc_free.restype = None
@@ -174,18 +176,24 @@ class Index:
         a = lib().orc_pattern_align(self.h, _ptr(r), r.size, t, _ptr(sums))
         return int(a), sums
 
-    def seed(self, reads: np.ndarray, offsets: np.ndarray, t: int, threads: int = 1):
-        """Sorted anchors (structured array) and per-read alignment indices."""
+    def seed(self, reads: np.ndarray, offsets: np.ndarray, t: int, threads: int = 1, seg_len: int = 0):
+        """Sorted anchors (structured array) and the alignment indices: one per
+        read, or with seg_len > 0 one per segment (reads longer than seg_len
+        bases are seeded in segments of seg_len; read order, then segment)."""
         reads = _bytes(reads)
         offs = np.ascontiguousarray(offsets, dtype=np.uint64)
         n = offs.size - 1
-        shifts = np.zeros(max(n, 1), np.uint32)
+        lens = np.diff(offs)
+        nseg = np.where((seg_len > 0) & (lens > seg_len), (lens + max(seg_len, 1) - 1) // max(seg_len, 1), 1)
+        n_sh = int(nseg.sum()) if n else 0
+        shifts = np.zeros(max(n_sh, 1), np.uint32)
         cnt = C.c_uint64(0)
-        buf = lib().orc_seed(self.h, _ptr(reads), _ptr(offs), n, t, threads, C.byref(cnt), _ptr(shifts))
+        buf = lib().orc_seed_segments(self.h, _ptr(reads), _ptr(offs), n, t, threads, seg_len, C.byref(cnt),
+                                      _ptr(shifts))
         m = int(cnt.value)
         arr = np.ctypeslib.as_array(buf, shape=(max(m, 1) * 4,))[: m * 4].copy()
         lib().orc_free(C.cast(buf, C.c_void_p))
-        return arr.view(ANCHOR_DTYPE), shifts[:n]
+        return arr.view(ANCHOR_DTYPE), shifts[:n_sh]
 
 
 def vote(anchors, offsets, D: int, V: int, max_out: int):

@@ -290,14 +290,36 @@ bool anchor_less(const Anchor& a, const Anchor& b) {
   return a.strand < b.strand;
 }
 
+// Number of segments a read of `len` bases is seeded in: one when seg_len is 0
+// or the read is not longer, else ceil(len / seg_len).
+uint64_t n_segments(uint64_t len, uint64_t seg_len) {
+  if (seg_len == 0 || len <= seg_len) return 1;
+  return (len + seg_len - 1) / seg_len;
+}
+
+// Seeds reads [lo, hi). With seg_len > 0 a read longer than seg_len bases is
+// cut into consecutive segments [j * seg_len, (j + 1) * seg_len) (the last one
+// shorter), the way the paper splits ultra-long reads into segments of at most
+// 30,000 bases (Sec. 2.2.2); each segment is pattern-aligned (its own shift)
+// and seeded on its own like a read, and its anchors carry the read's id and
+// read positions in whole-read coordinates (segment start added). Shifts go to
+// shifts[first_seg[r] + j].
 void seed_range(const Index* idx, const uint8_t* reads, const uint64_t* offsets, uint32_t lo,
-                uint32_t hi, uint32_t t, std::vector<Anchor>& out, uint32_t* shifts) {
+                uint32_t hi, uint32_t t, uint64_t seg_len, const uint64_t* first_seg,
+                std::vector<Anchor>& out, uint32_t* shifts) {
   for (uint32_t r = lo; r < hi; ++r) {
     const uint8_t* q = reads + offsets[r];
     const uint64_t len = offsets[r + 1] - offsets[r];
-    const uint32_t a = pattern_align(idx, q, len, t, nullptr);
-    if (shifts) shifts[r] = a;
-    seed_read(idx, r, q, len, a, out);
+    const uint64_t ns = n_segments(len, seg_len);
+    for (uint64_t j = 0; j < ns; ++j) {
+      const uint64_t b = ns == 1 ? 0 : j * seg_len;
+      const uint64_t plen = ns == 1 ? len : std::min<uint64_t>(seg_len, len - b);
+      const uint32_t a = pattern_align(idx, q + b, plen, t, nullptr);
+      if (shifts) shifts[first_seg[r] + j] = a;
+      const size_t before = out.size();
+      seed_read(idx, r, q + b, plen, a, out);
+      for (size_t e = before; e < out.size(); ++e) out[e].read_pos += (uint32_t)b;
+    }
   }
 }
 
@@ -513,23 +535,30 @@ uint32_t orc_pattern_align(const void* h, const uint8_t* read, uint64_t len, uin
 }
 
 // Seeds reads [0, n) (CSR byte offsets, n + 1 entries) with `n_threads` host
-// threads over contiguous read shards (1 = the plain single-threaded oracle).
+// threads over contiguous read shards (1 = the plain single-threaded oracle),
+// cutting reads longer than seg_len into segments (0 = never; see seed_range).
 // Returns a malloc'ed array of 4*u32 anchors sorted by (read_id, ref_pos,
-// read_pos, strand) and its length; per-read alignment indices go to `shifts`.
-uint32_t* orc_seed(const void* h, const uint8_t* reads, const uint64_t* offsets, uint32_t n,
-                   uint32_t t, int n_threads, uint64_t* n_out, uint32_t* shifts) {
+// read_pos, strand) and its length; the alignment index of every segment goes
+// to `shifts` (read order, then segment order: one entry per read when
+// seg_len is 0).
+uint32_t* orc_seed_segments(const void* h, const uint8_t* reads, const uint64_t* offsets, uint32_t n,
+                            uint32_t t, int n_threads, uint64_t seg_len, uint64_t* n_out, uint32_t* shifts) {
   const Index* idx = static_cast<const Index*>(h);
   if (n_threads < 1) n_threads = 1;
   if ((uint32_t)n_threads > n) n_threads = n > 0 ? (int)n : 1;
+  std::vector<uint64_t> first_seg(n + 1, 0);
+  for (uint32_t r = 0; r < n; ++r)
+    first_seg[r + 1] = first_seg[r] + n_segments(offsets[r + 1] - offsets[r], seg_len);
   std::vector<std::vector<Anchor>> parts(n_threads);
   std::vector<std::thread> pool;
+  const uint64_t* fs = first_seg.data();
   for (int i = 0; i < n_threads; ++i) {
     const uint32_t lo = (uint32_t)((uint64_t)n * i / n_threads);
     const uint32_t hi = (uint32_t)((uint64_t)n * (i + 1) / n_threads);
     if (n_threads == 1) {
-      seed_range(idx, reads, offsets, lo, hi, t, parts[i], shifts);
+      seed_range(idx, reads, offsets, lo, hi, t, seg_len, fs, parts[i], shifts);
     } else {
-      pool.emplace_back([=, &parts]() { seed_range(idx, reads, offsets, lo, hi, t, parts[i], shifts); });
+      pool.emplace_back([=, &parts]() { seed_range(idx, reads, offsets, lo, hi, t, seg_len, fs, parts[i], shifts); });
     }
   }
   for (auto& th : pool) th.join();
@@ -540,6 +569,12 @@ uint32_t* orc_seed(const void* h, const uint8_t* reads, const uint64_t* offsets,
   uint32_t* buf = (uint32_t*)std::malloc(std::max<size_t>(1, all.size()) * sizeof(Anchor));
   if (!all.empty()) std::memcpy(buf, all.data(), all.size() * sizeof(Anchor));
   return buf;
+}
+
+// The same without segments (one alignment index per read).
+uint32_t* orc_seed(const void* h, const uint8_t* reads, const uint64_t* offsets, uint32_t n,
+                   uint32_t t, int n_threads, uint64_t* n_out, uint32_t* shifts) {
+  return orc_seed_segments(h, reads, offsets, n, t, n_threads, 0, n_out, shifts);
 }
 
 void orc_free(void* p) { std::free(p); }
