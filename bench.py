@@ -333,6 +333,27 @@ def time_events(stream, flush, fn, reps=3):
     return statistics.mean(tt)
 
 
+def vote_line(god, torch, dev, stream, flush, idx, d_reads, d_offs, bases, long_reads):
+    """Location voting over one seeding result on the device: D = 100, V = 3
+    and 8 winners per read for long reads, D = 50, V = 2 and 4 for short
+    ones (Sec. 3.4 steps 4 / 5)."""
+    D, V, max_out = (100, 3, 8) if long_reads else (50, 2, 4)
+    ptr, m = god.god_seed_device(idx, d_reads, d_offs, stream=stream)
+    n = d_offs.numel() - 1
+    d_out = torch.empty((n * max_out, 10), dtype=torch.int32, device=dev)
+    d_cnt = torch.empty(n, dtype=torch.int32, device=dev)
+
+    def vote():
+        god.god_vote((ptr, m), d_offs, D, V, max_out, out=d_out, counts=d_cnt, stream=stream)
+
+    vote()
+    ms = time_events(stream, flush, vote)
+    winners = int(d_cnt.sum().item())
+    god.god_free(ptr)
+    return {"D": D, "V": V, "max_out": max_out, "anchors": m, "ms": ms, "anchors_per_s": m / (ms / 1e3),
+            "read_bases_per_s": bases / (ms / 1e3), "records": winners}
+
+
 def workload_line(god, torch, dev, stream, flush, name, ref=None):
     """Seeding throughput of one stated workload at its full size with a resident
     index (inputs in HBM), hash against learned lookups, plus each index's build
@@ -373,6 +394,21 @@ def workload_line(god, torch, dev, stream, flush, name, ref=None):
         info = idx.info
         out[nm] = {"read_bases_per_s": bases / (ms / 1e3), "anchors_per_s": res["m"] / (ms / 1e3),
                    "anchors": res["m"], "seed_ms": ms, "index_build_ms": build_ms}
+        if nm == "hash":
+            out["vote"] = vote_line(god, torch, dev, stream, flush, idx, d_reads, d_offs, bases, long_reads=True)
+            if wl.lengths.kind != "fixed":
+                seg = {}
+
+                def seed_seg():
+                    ptr, m = god.god_seed_device(idx, d_reads, d_offs, stream=stream, seg_len=30_000)
+                    seg["m"] = m
+                    god.god_free(ptr)
+
+                seed_seg()
+                sms = time_events(stream, flush, seed_seg)
+                out["segmented_30kb"] = {"read_bases_per_s": bases / (sms / 1e3), "anchors": seg["m"],
+                                         "seed_ms": sms, "note": "hash index, reads cut into 30,000-base "
+                                                                 "segments, each pattern-aligned on its own"}
         if nm == "learned":
             out[nm].update(rmi_mean_eps=info["rmi_mean_eps"], rmi_leaves=info["rmi_leaves"],
                            rmi_fallback_key_frac=info["rmi_fallback_key_frac"])
@@ -574,6 +610,9 @@ def main():
             info = idx.info
             seed_only[nm] = {"read_bases_per_s": bases / (statistics.mean(tt) / 1e3),
                              "ms": statistics.mean(tt)}
+            if nm == "hash":
+                seed_only["vote"] = vote_line(god, torch, dev, stream, flush, idx, d_reads, d_offs, bases,
+                                              long_reads=False)
             if nm == "learned":
                 seed_only[nm].update(rmi_mean_eps=info["rmi_mean_eps"], rmi_leaves=info["rmi_leaves"],
                                      rmi_fallback_key_frac=info["rmi_fallback_key_frac"])

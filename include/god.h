@@ -157,7 +157,14 @@ typedef struct {
   void *stream;            /* cudaStream_t; NULL = legacy default stream */
   uint32_t pa_t;           /* overrides the index's t when != UINT32_MAX */
   int via;                 /* -1 = the index's kind, 0 = hash, 1 = learned */
-  uint32_t *shifts_out;    /* optional host/device array of n alignment indices */
+  uint32_t *shifts_out;    /* optional host/device array of alignment indices: one per read, or one per
+                              segment when seg_len > 0 (read order, then segment order) */
+  uint32_t seg_len;        /* 0 = off (default). Otherwise a read longer than seg_len bases is cut into
+                              ceil(len / seg_len) consecutive segments of seg_len bases (the last one
+                              shorter), as the paper splits ultra-long reads into segments of at most
+                              30,000 bases (Sec. 2.2.2); each segment is pattern-aligned on its own
+                              (Sec. 3.2) and seeded; its anchors keep the read's id and whole-read
+                              positions, and each read's list stays sorted as above */
 } god_seed_opts;
 
 void god_seed_opts_init(god_seed_opts *o);

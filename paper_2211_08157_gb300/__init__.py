@@ -127,10 +127,12 @@ def god_index_lookup(index: GodIndex, keys, via: int = 0, stream=None):
     return count, first
 
 
-def _opts(stream=None, pa_t=None, via=None, shifts_out=None) -> SeedOpts:
+def _opts(stream=None, pa_t=None, via=None, shifts_out=None, seg_len=None) -> SeedOpts:
     o = SeedOpts()
     load().god_seed_opts_init(C.byref(o))
     o.stream = _stream_ptr(stream)
+    if seg_len is not None:
+        o.seg_len = seg_len
     if pa_t is not None:
         o.pa_t = pa_t
     if via is not None:
@@ -163,14 +165,15 @@ def god_seed(index: GodIndex, reads, offsets):
     return _owned_anchors(ptr, cnt.value)
 
 
-def god_seed_into(index: GodIndex, reads, offsets, out, stream=None, pa_t=None, via=None, shifts_out=None) -> int:
+def god_seed_into(index: GodIndex, reads, offsets, out, stream=None, pa_t=None, via=None, shifts_out=None,
+                  seg_len=None) -> int:
     """Anchors written into `out` (host numpy or device tensor of 16-byte rows); returns the count.
     Raises GodError(rc=GOD_ERANGE) with the needed count when `out` is too small."""
     reads = _u8(reads)
     n = (offsets.size if isinstance(offsets, np.ndarray) else offsets.numel()) - 1
     cap = (out.nbytes if isinstance(out, np.ndarray) else out.numel() * out.element_size()) // 16
     cnt = C.c_uint64()
-    o = _opts(stream, pa_t, via, shifts_out)
+    o = _opts(stream, pa_t, via, shifts_out, seg_len)
     rc = load().god_seed_into(index.h, _ptr(reads), _ptr(offsets), n, _ptr(out), cap, C.byref(cnt), C.byref(o))
     if rc == -5:
         err = GodError(rc, f"output holds {cap} anchors, {cnt.value} needed")
@@ -180,12 +183,13 @@ def god_seed_into(index: GodIndex, reads, offsets, out, stream=None, pa_t=None, 
     return cnt.value
 
 
-def god_seed_device(index: GodIndex, d_reads, d_offsets, stream=None, pa_t=None, via=None, shifts_out=None):
+def god_seed_device(index: GodIndex, d_reads, d_offsets, stream=None, pa_t=None, via=None, shifts_out=None,
+                    seg_len=None):
     """Device inputs (torch CUDA tensors) -> (device pointer, count); free with god_free."""
     n = d_offsets.numel() - 1
     ptr = C.c_void_p()
     cnt = C.c_uint64()
-    o = _opts(stream, pa_t, via, shifts_out)
+    o = _opts(stream, pa_t, via, shifts_out, seg_len)
     check(load().god_seed_device(index.h, _ptr(d_reads), _ptr(d_offsets), n, C.byref(ptr), C.byref(cnt),
                                  C.byref(o)))
     return ptr.value, cnt.value

@@ -19,7 +19,8 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libgod.so")
 INCLUDE = os.path.join(ROOT, "include")
-SOURCES = ["api.cu", "scan.cu", "sketch.cu", "radix.cu", "index.cu", "rmi.cu", "seed.cu", "serve.cu", "vote.cu"]
+SOURCES = ["api.cu", "scan.cu", "sketch.cu", "radix.cu", "index.cu", "rmi.cu", "seed.cu", "serve.cu", "vote.cu",
+           "segment.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
               "-Xcompiler", "-Wall", "-I", INCLUDE]
@@ -84,7 +85,8 @@ class Params(C.Structure):
 
 
 class SeedOpts(C.Structure):
-    _fields_ = [("stream", C.c_void_p), ("pa_t", C.c_uint32), ("via", C.c_int), ("shifts_out", C.c_void_p)]
+    _fields_ = [("stream", C.c_void_p), ("pa_t", C.c_uint32), ("via", C.c_int), ("shifts_out", C.c_void_p),
+                ("seg_len", C.c_uint32)]
 
 
 class IndexInfo(C.Structure):

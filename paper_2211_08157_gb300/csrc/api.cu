@@ -586,6 +586,9 @@ static int seed_common(const god_index* idx, const uint8_t* reads, const uint64_
     GOD_TRY(to_device(offsets, (uint64_t)(n + 1) * 8, hold_off, &doff, st));
   }
   GOD_TRY(to_device(reads, bytes, hold_reads, &dreads, st));
+  if (o.seg_len > 0)
+    return seed_segmented(idx, (const uint8_t*)dreads, (const uint64_t*)doff, n, bytes, o, st, d_alloc, n_anchors,
+                          user_dev, user_cap, true);
   return seed_device(idx, (const uint8_t*)dreads, (const uint64_t*)doff, n, bytes, o, st, d_alloc, n_anchors,
                      user_dev, user_cap, true);
 }

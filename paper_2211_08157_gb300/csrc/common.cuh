@@ -295,7 +295,11 @@ int rmi_root_grad_device(const float* d_theta, int H, const float* d_x, const fl
 int seed_device(const god_index* idx, const uint8_t* d_reads, const uint64_t* d_offsets, uint32_t n,
                 uint64_t read_bytes, const god_seed_opts& o, cudaStream_t st, god_anchor** d_out,
                 uint64_t* n_anchors, god_anchor* user_out, uint64_t user_cap, bool user_out_device);
-// Location voting over device arrays (see god_vote_rec).
+// seed_device with reads longer than o.seg_len seeded in segments (god_seed_opts.seg_len).
+int seed_segmented(const god_index* idx, const uint8_t* d_reads, const uint64_t* d_offsets, uint32_t n,
+                   uint64_t read_bytes, const god_seed_opts& o, cudaStream_t st, god_anchor** d_out,
+                   uint64_t* n_anchors, god_anchor* user_out, uint64_t user_cap, bool user_out_device);
+// Location voting over device arrays (see god_vote).
 int vote_device(const god_anchor* d_a, uint64_t m, const uint64_t* d_offs, uint32_t n, const god_vote_params& p,
                 god_vote_rec* d_out, uint32_t* d_counts, cudaStream_t st);
 }  // namespace god
