@@ -8,7 +8,8 @@ Every function mirrors one step of the method (paper sections in the C++ file):
 sparsification (Sec. 3, 3.2), the Wang integer hash (Sec. 3.6.1), (w,k)-minimizers
 (Sec. 3.1), the filtered seed index (Sec. 3.1, 3.2), pattern alignment (Sec. 3.2),
 compressed seeding to sorted anchors (Sec. 3.3), location voting with the rescue
-location (Sec. 3.4, Sec. 3.6.3), and the learned-index reference.
+location (Sec. 3.4, Sec. 3.6.3), containment search (Sec. 2.3), and the
+learned-index reference.
 """
 from __future__ import annotations
 
@@ -72,6 +73,9 @@ def lib():
             L.orc_seed_segments.argtypes = [p, p, p, u32, u32, i32, u64, C.POINTER(u64), p]
             L.orc_vote.restype = i32
             L.orc_vote.argtypes = [p, u64, p, u32, u32, u32, u32, p, p]
+            L.orc_contain.restype = i32
+            L.orc_contain.argtypes = [p, p, u32, p, u32, p, p, u32, C.c_char_p, i32, i32, u32, u32, u32, u32, u64,
+                                      i32, p, p, p, p]
             L.orc_free.restype = None
             L.orc_free.argtypes = [p]
             L.orc_root_loss_grad_f64.restype = C.c_double
@@ -211,6 +215,28 @@ def vote(anchors, offsets, D: int, V: int, max_out: int):
     counts = counts[:n]
     keep = (np.arange(max_out)[None, :] < counts[:, None]).reshape(-1)
     return out[: n * max_out][keep], counts
+
+
+def contain(db, contig_offsets, contig_genome, n_genomes: int, reads, read_offsets, pattern: str, k: int, w: int,
+            max_occ: int, t: int, D: int, V: int, batch_bases: int, threads: int = 1):
+    """Containment search (Sec. 2.3): (read genome (-1 = unmapped), read votes,
+    genome mapped reads, genome mapped read bases)."""
+    dbb = _bytes(db)
+    co = np.ascontiguousarray(contig_offsets, dtype=np.uint64)
+    cg = np.ascontiguousarray(contig_genome, dtype=np.uint32)
+    rb = _bytes(reads)
+    ro = np.ascontiguousarray(read_offsets, dtype=np.uint64)
+    nr = ro.size - 1
+    rg = np.zeros(max(nr, 1), np.int32)
+    rv = np.zeros(max(nr, 1), np.uint32)
+    gr = np.zeros(max(n_genomes, 1), np.uint64)
+    gb = np.zeros(max(n_genomes, 1), np.uint64)
+    rc = lib().orc_contain(_ptr(dbb), _ptr(co), co.size - 1, _ptr(cg), n_genomes, _ptr(rb), _ptr(ro), nr,
+                           pattern.encode(), k, w, max_occ, t, D, V, batch_bases, threads, _ptr(rg), _ptr(rv),
+                           _ptr(gr), _ptr(gb))
+    if rc != 0:
+        raise ValueError("bad pattern or genome id")
+    return rg[:nr], rv[:nr], gr[:n_genomes], gb[:n_genomes]
 
 
 def root_loss_grad_f64(theta: np.ndarray, H: int, x: np.ndarray, y: np.ndarray):

@@ -17,6 +17,8 @@
 //   * pattern alignment (Sec. 3.2) and compressed seeding to anchors (Sec. 3.3);
 //   * location voting on each read's anchors, with the rescue location
 //     (Sec. 3.4, Fig. 8, Sec. 3.6.3);
+//   * containment search over a database of genomes indexed on the fly in
+//     batches (Sec. 2.3);
 //   * the learned-index (RMI) reference: MLP root forward/backward, leaf least
 //     squares and per-leaf error bounds in the same FP32 operation order the GPU
 //     lookup uses.
@@ -402,6 +404,91 @@ void vote_read(uint32_t read_id, const Anchor* a, size_t n, uint64_t len, uint32
   out.insert(out.end(), win.begin(), win.end());
 }
 
+// ---------------------------------------------------------------- containment search
+// Sec. 2.3: reads are mapped against a database of genomes whose index is
+// built on the fly, in batches of at most batch_bases bases, without a
+// pre-built index; a mapped read is one that receives a mapping location from
+// location voting; a genome is reported when it has enough mapped reads and
+// enough coverage. Readings where the paper is silent:
+//   * a batch lays its contigs end to end, each starting at a multiple of the
+//     pattern length p after at least one N (base_{j+1} = roundup(base_j +
+//     len_j + 1, p)), so every contig is sparsified from its own start and no
+//     k-mer spans two contigs; contigs join a batch in database order while
+//     the batch's length stays <= batch_bases (a batch holds at least one);
+//   * a read's location in a batch is its first voting record when it is a
+//     winner (votes >= V; a rescue record is not a mapping location here);
+//     its genome is that of the contig holding ref_lo; over all batches the
+//     location with the most votes counts, the earlier batch on ties;
+//   * coverage of a genome = mapped read bases / the genome's contig bases.
+struct ContainOut {
+  std::vector<int32_t> read_genome;
+  std::vector<uint32_t> read_votes;
+};
+
+void contain(const uint8_t* db, const uint64_t* coff, uint32_t n_contigs, const uint32_t* cgen, const uint8_t* reads,
+             const uint64_t* roff, uint32_t n_reads, const std::vector<int>& P, int k, int w, uint32_t max_occ,
+             uint32_t t, uint32_t D, uint32_t V, uint64_t batch_bases, int threads, ContainOut& out) {
+  const uint64_t p = P.size();
+  out.read_genome.assign(n_reads, -1);
+  out.read_votes.assign(n_reads, 0);
+  uint32_t j0 = 0;
+  while (j0 < n_contigs) {
+    // contigs [j0, j1) and their start positions in the batch
+    std::vector<uint64_t> base;
+    uint64_t end = 0;
+    uint32_t j1 = j0;
+    while (j1 < n_contigs) {
+      const uint64_t b = base.empty() ? 0 : ((end + 1 + p - 1) / p) * p;
+      const uint64_t e = b + (coff[j1 + 1] - coff[j1]);
+      if (!base.empty() && e > batch_bases) break;
+      base.push_back(b);
+      end = e;
+      ++j1;
+    }
+    std::vector<uint8_t> ref(end, 'N');
+    for (uint32_t j = j0; j < j1; ++j)
+      std::memcpy(ref.data() + base[j - j0], db + coff[j], coff[j + 1] - coff[j]);
+    Index* idx = build_index(ref.data(), ref.size(), P, k, w, max_occ);
+    std::vector<uint32_t> shifts(n_reads);
+    std::vector<std::vector<Anchor>> parts(std::max(1, threads));
+    std::vector<uint64_t> first_seg(n_reads + 1);
+    for (uint32_t r = 0; r <= n_reads; ++r) first_seg[r] = r;
+    {
+      std::vector<std::thread> pool;
+      const int nt = std::max(1, threads);
+      for (int i = 0; i < nt; ++i) {
+        const uint32_t lo = (uint32_t)((uint64_t)n_reads * i / nt), hi = (uint32_t)((uint64_t)n_reads * (i + 1) / nt);
+        pool.emplace_back([&, lo, hi, i]() {
+          seed_range(idx, reads, roff, lo, hi, t, 0, first_seg.data(), parts[i], shifts.data());
+        });
+      }
+      for (auto& th : pool) th.join();
+    }
+    std::vector<Anchor> all;
+    for (auto& v : parts) all.insert(all.end(), v.begin(), v.end());
+    std::sort(all.begin(), all.end(), anchor_less);
+    size_t i = 0;
+    while (i < all.size()) {
+      const uint32_t r = all[i].read_id;
+      size_t e = i;
+      while (e < all.size() && all[e].read_id == r) ++e;
+      std::vector<VoteRec> res;
+      vote_read(r, all.data() + i, e - i, roff[r + 1] - roff[r], D, V, 1, res);
+      if (!res.empty() && !res[0].rescue && res[0].votes > out.read_votes[r]) {
+        const uint64_t pos = res[0].ref_lo;
+        uint32_t c = j0;
+        for (uint32_t j = j0; j < j1; ++j)
+          if (base[j - j0] <= pos) c = j;
+        out.read_votes[r] = res[0].votes;
+        out.read_genome[r] = (int32_t)cgen[c];
+      }
+      i = e;
+    }
+    delete idx;
+    j0 = j1;
+  }
+}
+
 // ---------------------------------------------------------------- RMI reference
 // Learned index over the sorted kept keys: a root MLP 1 -> H -> 1 (ReLU) maps the
 // normalised key to a leaf; each leaf holds a linear model of the rank. The
@@ -732,6 +819,32 @@ int orc_vote(const uint32_t* anchors, uint64_t n_anchors, const uint64_t* offset
     counts[r] = (uint32_t)res.size();
     std::memcpy(out + (uint64_t)r * max_out * 10, res.data(), res.size() * sizeof(VoteRec));
     i = j;
+  }
+  return 0;
+}
+
+
+// Containment search (see contain): per read its genome (-1 = unmapped) and
+// votes; per genome its mapped reads and mapped read bases. Returns 0, or -1
+// on a bad pattern or a contig genome id >= n_genomes.
+int orc_contain(const uint8_t* db, const uint64_t* coff, uint32_t n_contigs, const uint32_t* cgen, uint32_t n_genomes,
+                const uint8_t* reads, const uint64_t* roff, uint32_t n_reads, const char* pattern, int k, int w,
+                uint32_t max_occ, uint32_t t, uint32_t D, uint32_t V, uint64_t batch_bases, int threads,
+                int32_t* read_genome, uint32_t* read_votes, uint64_t* genome_reads, uint64_t* genome_bases) {
+  std::vector<int> P;
+  if (!parse_pattern(pattern, P)) return -1;
+  for (uint32_t j = 0; j < n_contigs; ++j)
+    if (cgen[j] >= n_genomes) return -1;
+  ContainOut o;
+  contain(db, coff, n_contigs, cgen, reads, roff, n_reads, P, k, w, max_occ, t, D, V, batch_bases, threads, o);
+  for (uint32_t g = 0; g < n_genomes; ++g) genome_reads[g] = genome_bases[g] = 0;
+  for (uint32_t r = 0; r < n_reads; ++r) {
+    read_genome[r] = o.read_genome[r];
+    read_votes[r] = o.read_votes[r];
+    if (o.read_genome[r] >= 0) {
+      genome_reads[o.read_genome[r]] += 1;
+      genome_bases[o.read_genome[r]] += roff[r + 1] - roff[r];
+    }
   }
   return 0;
 }
