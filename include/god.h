@@ -273,6 +273,47 @@ typedef struct {
 int god_vote(const god_anchor *anchors, uint64_t n_anchors, const uint64_t *offsets, uint32_t n_reads,
              const god_vote_params *params, god_vote_rec *out, uint32_t *counts, void *stream);
 
+/* ----------------------------------------------------------------- containment search
+ * god_contain: containment search (Sec. 2.3) of a read set against a database
+ * of genomes, without a pre-built index: the database is indexed on the fly in
+ * batches of at most batch_bases bases; every read is seeded against each
+ * batch (pattern alignment, compressed seeding) and location voting (with D,
+ * V) gives its best location there; over all batches a read keeps the winner
+ * with the most votes (the earlier batch on ties; a rescue location is not a
+ * mapping location here), and each genome counts the reads and read bases
+ * mapped to it. A genome's coverage is its mapped read bases / its contig
+ * bases; the paper reports genomes with enough mapped reads and coverage >= 1.
+ * A batch lays its contigs end to end, each starting at a multiple of the
+ * pattern length after at least one N, so every contig is sparsified from its
+ * own start and no k-mer spans two contigs; contigs join a batch in database
+ * order while its length stays <= batch_bases (at least one per batch; each
+ * batch < 2^32 bases).
+ *   db              host or device, the contigs' bases back to back.
+ *   contig_offsets  host, n_contigs + 1 byte offsets into db.
+ *   contig_genome   host, n_contigs genome ids < n_genomes.
+ *   reads, read_offsets  host or device, as for god_seed.
+ *   read_genome     host, n_reads: genome of each read's location, -1 = unmapped.
+ *   read_votes      host, n_reads: votes of that location (0 = unmapped).
+ *   genome_reads, genome_bases  host, n_genomes: mapped reads and read bases.
+ * Errors: GOD_EINVAL (bad pattern, k, w, V, a genome id out of range,
+ * decreasing offsets), GOD_ENOMEM, GOD_ECUDA, GOD_ETIMEOUT. Synchronous. */
+typedef struct {
+  const char *pattern;     /* default "10" (the paper's containment runs) */
+  int k, w;                /* default 28, 40 */
+  uint32_t max_occ;        /* default 1000 */
+  uint32_t pa_t;           /* pattern alignment minimizers per shift, default 32 */
+  uint32_t D, V;           /* location voting, default 100, 3 */
+  int index_kind;          /* GOD_INDEX_HASH (default) or GOD_INDEX_LEARNED */
+  uint64_t batch_bases;    /* default 2^32 - 1 */
+} god_contain_params;
+
+void god_contain_params_init(god_contain_params *p);
+int god_contain(const uint8_t *db, const uint64_t *contig_offsets, uint32_t n_contigs,
+                const uint32_t *contig_genome, uint32_t n_genomes, const uint8_t *reads,
+                const uint64_t *read_offsets, uint32_t n_reads, const god_contain_params *params,
+                int32_t *read_genome, uint32_t *read_votes, uint64_t *genome_reads, uint64_t *genome_bases,
+                void *stream);
+
 /* ----------------------------------------------------------------- learned index
  * Gradient of the root MLP's mean squared error (1 -> H -> 1, ReLU; parameter
  * layout W1[H], b1[H], W2[H], b2) over samples (x[i], y[i]), computed by the

@@ -14,8 +14,8 @@ import weakref
 import numpy as np
 
 from . import _lib
-from ._lib import (GodError, IndexInfo, Params, SeedOpts, ServerConfig, ServerStats, VoteParams, build, check,
-                   load)
+from ._lib import (ContainParams, GodError, IndexInfo, Params, SeedOpts, ServerConfig, ServerStats, VoteParams,
+                   build, check, load)
 
 ANCHOR_DTYPE = np.dtype([("read_id", "<u4"), ("read_pos", "<u4"), ("ref_pos", "<u4"), ("strand", "<u4")])
 VOTE_DTYPE = np.dtype([("read_id", "<u4"), ("votes", "<u4"), ("strand", "<u4"), ("rescue", "<u4"), ("loc", "<i8"),
@@ -244,6 +244,31 @@ def god_vote(anchors, offsets, D: int, V: int, max_out: int, out=None, counts=No
     cnt = cnt[:n]
     keep = (np.arange(max_out)[None, :] < cnt[:, None]).reshape(-1)
     return rec[: n * max_out][keep], cnt
+
+
+def god_contain(db, contig_offsets, contig_genome, n_genomes: int, reads, read_offsets, pattern: str = "10",
+                k: int = 28, w: int = 40, max_occ: int = 1000, pa_t: int = 32, D: int = 100, V: int = 3,
+                batch_bases: int = (1 << 32) - 1, index_kind: int = GOD_INDEX_HASH, stream=None):
+    """Containment search (god_contain): (read genome (-1 = unmapped), read
+    votes, genome mapped reads, genome mapped read bases)."""
+    L = load()
+    prm = ContainParams()
+    L.god_contain_params_init(C.byref(prm))
+    pat = pattern.encode()
+    prm.pattern, prm.k, prm.w, prm.max_occ, prm.pa_t = pat, k, w, max_occ, pa_t
+    prm.D, prm.V, prm.batch_bases, prm.index_kind = D, V, batch_bases, index_kind
+    db = _u8(db)
+    co = np.ascontiguousarray(contig_offsets, dtype=np.uint64)
+    cg = np.ascontiguousarray(contig_genome, dtype=np.uint32)
+    reads = _u8(reads)
+    nr = _numel(read_offsets) - 1
+    rg = np.zeros(max(nr, 1), np.int32)
+    rv = np.zeros(max(nr, 1), np.uint32)
+    gr = np.zeros(max(n_genomes, 1), np.uint64)
+    gb = np.zeros(max(n_genomes, 1), np.uint64)
+    check(L.god_contain(_ptr(db), _ptr(co), co.size - 1, _ptr(cg), n_genomes, _ptr(reads), _ptr(read_offsets), nr,
+                        C.byref(prm), _ptr(rg), _ptr(rv), _ptr(gr), _ptr(gb), _stream_ptr(stream)))
+    return rg[:nr], rv[:nr], gr[:n_genomes], gb[:n_genomes]
 
 
 def god_rmi_root_grad(theta, H: int, x, y):

@@ -20,7 +20,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libgod.so")
 INCLUDE = os.path.join(ROOT, "include")
 SOURCES = ["api.cu", "scan.cu", "sketch.cu", "radix.cu", "index.cu", "rmi.cu", "seed.cu", "serve.cu", "vote.cu",
-           "segment.cu"]
+           "segment.cu", "contain.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
               "-Xcompiler", "-Wall", "-I", INCLUDE]
@@ -102,6 +102,12 @@ class VoteParams(C.Structure):
     _fields_ = [("D", C.c_uint32), ("V", C.c_uint32), ("max_out", C.c_uint32)]
 
 
+class ContainParams(C.Structure):
+    _fields_ = [("pattern", C.c_char_p), ("k", C.c_int), ("w", C.c_int), ("max_occ", C.c_uint32),
+                ("pa_t", C.c_uint32), ("D", C.c_uint32), ("V", C.c_uint32), ("index_kind", C.c_int),
+                ("batch_bases", C.c_uint64)]
+
+
 class ServerConfig(C.Structure):
     _fields_ = [("slots", C.c_int), ("mem_budget", C.c_uint64), ("max_batch_bases", C.c_uint64)]
 
@@ -130,6 +136,8 @@ SIGNATURES = {
     "god_sketch_noalloc": (I32, [P_, U64, C.c_char_p, U32, I32, I32, P_, U64, C.POINTER(U64), P_]),
     "god_rmi_root_grad": (I32, [P_, I32, P_, P_, U64, P_, P_]),
     "god_vote": (I32, [P_, U64, P_, U32, C.POINTER(VoteParams), P_, P_, P_]),
+    "god_contain_params_init": (None, [C.POINTER(ContainParams)]),
+    "god_contain": (I32, [P_, P_, U32, P_, U32, P_, P_, U32, C.POINTER(ContainParams), P_, P_, P_, P_, P_]),
     "god_free": (None, [P_]),
     "god_launch_count": (U64, []),
     "god_prof_enable": (None, [I32]),

@@ -718,6 +718,70 @@ int god_vote(const god_anchor* anchors, uint64_t n_anchors, const uint64_t* offs
   return GOD_OK;
 }
 
+void god_contain_params_init(god_contain_params* p) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  p->pattern = "10";
+  p->k = 28;
+  p->w = 40;
+  p->max_occ = 1000;
+  p->pa_t = 32;
+  p->D = 100;
+  p->V = 3;
+  p->index_kind = GOD_INDEX_HASH;
+  p->batch_bases = (1ull << 32) - 1;
+}
+
+int god_contain(const uint8_t* db, const uint64_t* contig_offsets, uint32_t n_contigs, const uint32_t* contig_genome,
+                uint32_t n_genomes, const uint8_t* reads, const uint64_t* read_offsets, uint32_t n_reads,
+                const god_contain_params* params, int32_t* read_genome, uint32_t* read_votes, uint64_t* genome_reads,
+                uint64_t* genome_bases, void* stream) {
+  if (!params || !contig_offsets || (n_contigs && !contig_genome) || (n_reads && (!read_offsets || !reads)) ||
+      (n_reads && (!read_genome || !read_votes)) || (n_genomes && (!genome_reads || !genome_bases))) {
+    set_error("god_contain: null argument");
+    return GOD_EINVAL;
+  }
+  PatternInfo P;
+  if (parse_pattern(params->pattern, &P) != GOD_OK || params->k < 1 || params->k > 28 || params->w < 1 ||
+      params->w > 255 || params->V < 1 || params->max_occ < 1 || params->batch_bases == 0) {
+    set_error("god_contain: bad pattern, k, w, max_occ, V or batch size");
+    return GOD_EINVAL;
+  }
+  if (is_device_ptr(contig_offsets) || is_device_ptr(contig_genome)) {
+    set_error("god_contain: contig offsets and genome ids must be host arrays");
+    return GOD_EINVAL;
+  }
+  for (uint32_t j = 0; j < n_contigs; ++j) {
+    if (contig_genome[j] >= n_genomes || contig_offsets[j + 1] < contig_offsets[j]) {
+      set_error("god_contain: genome id out of range or decreasing contig offsets");
+      return GOD_EINVAL;
+    }
+  }
+  if (contig_offsets[n_contigs] > contig_offsets[0] && !db) {
+    set_error("god_contain: null database");
+    return GOD_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  DBuf<uint8_t> hold_off, hold_reads;
+  const void* doff = nullptr;
+  const void* dreads = nullptr;
+  uint64_t bytes = 0;
+  if (n_reads) {
+    if (is_device_ptr(read_offsets)) {
+      doff = read_offsets;
+      GOD_CK(cudaMemcpyAsync(&bytes, read_offsets + n_reads, 8, cudaMemcpyDeviceToHost, st));
+      GOD_CK(cudaStreamSynchronize(st));
+    } else {
+      bytes = read_offsets[n_reads];
+      GOD_TRY(to_device(read_offsets, ((uint64_t)n_reads + 1) * 8, hold_off, &doff, st));
+    }
+    GOD_TRY(to_device(reads, bytes, hold_reads, &dreads, st));
+  }
+  return contain_device(db, is_device_ptr(db), contig_offsets, n_contigs, contig_genome, n_genomes,
+                        (const uint8_t*)dreads, (const uint64_t*)doff, n_reads, bytes, *params, read_genome,
+                        read_votes, genome_reads, genome_bases, st);
+}
+
 int god_rmi_root_grad(const float* theta, int H, const float* x, const float* y, uint64_t n, float* grad, float* loss) {
   if (!theta || !grad || !loss || (n && (!x || !y)) || H != kRootHidden) return GOD_EINVAL;
   const int np = 3 * H + 1;

@@ -299,6 +299,11 @@ int seed_device(const god_index* idx, const uint8_t* d_reads, const uint64_t* d_
 int seed_segmented(const god_index* idx, const uint8_t* d_reads, const uint64_t* d_offsets, uint32_t n,
                    uint64_t read_bytes, const god_seed_opts& o, cudaStream_t st, god_anchor** d_out,
                    uint64_t* n_anchors, god_anchor* user_out, uint64_t user_cap, bool user_out_device);
+// Containment search (see god_contain); reads and read offsets on the device.
+int contain_device(const uint8_t* db, bool db_on_device, const uint64_t* coff, uint32_t n_contigs, const uint32_t* cgen,
+                   uint32_t n_genomes, const uint8_t* d_reads, const uint64_t* d_roff, uint32_t n_reads,
+                   uint64_t read_bytes, const god_contain_params& prm, int32_t* h_read_genome,
+                   uint32_t* h_read_votes, uint64_t* h_genome_reads, uint64_t* h_genome_bases, cudaStream_t st);
 // Location voting over device arrays (see god_vote).
 int vote_device(const god_anchor* d_a, uint64_t m, const uint64_t* d_offs, uint32_t n, const god_vote_params& p,
                 god_vote_rec* d_out, uint32_t* d_counts, cudaStream_t st);

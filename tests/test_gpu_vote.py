@@ -93,7 +93,7 @@ def test_vote_seeded_short_reads(god):
         assert np.array_equal(gc, wc) and np.array_equal(got, want)
     # most reads vote for their true start (forward) on the true strand
     first = np.zeros(offs.size - 1, np.int64) - 1
-    starts = np.concatenate([[0], np.cumsum(gc)[:-1]])
+    starts = np.concatenate([[0], np.cumsum(gc.astype(np.int64))[:-1]]).astype(np.int64)
     has = gc > 0
     first[has] = got["loc"][starts[has]]
     fwd = (truth["strand"] == 0) & has
