@@ -8,8 +8,8 @@ Every function mirrors one step of the method (paper sections in the C++ file):
 sparsification (Sec. 3, 3.2), the Wang integer hash (Sec. 3.6.1), (w,k)-minimizers
 (Sec. 3.1), the filtered seed index (Sec. 3.1, 3.2), pattern alignment (Sec. 3.2),
 compressed seeding to sorted anchors (Sec. 3.3), location voting with the rescue
-location (Sec. 3.4, Sec. 3.6.3), containment search (Sec. 2.3), and the
-learned-index reference.
+location (Sec. 3.4, Sec. 3.6.3), containment search (Sec. 2.3), the seed matching
+evaluation (Sec. 2.1.1), and the learned-index reference.
 """
 from __future__ import annotations
 
@@ -76,6 +76,8 @@ def lib():
             L.orc_contain.restype = i32
             L.orc_contain.argtypes = [p, p, u32, p, u32, p, p, u32, C.c_char_p, i32, i32, u32, u32, u32, u32, u64,
                                       i32, p, p, p, p]
+            L.orc_seed_match.restype = i32
+            L.orc_seed_match.argtypes = [p, p, u32, C.c_char_p, C.c_char_p, i32, i32, p, p, p]
             L.orc_free.restype = None
             L.orc_free.argtypes = [p]
             L.orc_root_loss_grad_f64.restype = C.c_double
@@ -237,6 +239,26 @@ def contain(db, contig_offsets, contig_genome, n_genomes: int, reads, read_offse
     if rc != 0:
         raise ValueError("bad pattern or genome id")
     return rg[:nr], rv[:nr], gr[:n_genomes], gb[:n_genomes]
+
+
+SEED_KINDS = ("all", "minimizer", "spaced", "god")
+
+
+def seed_match(seqs, offsets, pattern: str, spaced: str, k: int, w: int):
+    """Seed matching evaluation (Sec. 2.1.1): pair i = (seq 2i, seq 2i + 1).
+    Returns (Levenshtein distance [n], matched [n, 4], total [n, 4]) with the
+    columns in SEED_KINDS order."""
+    sb = _bytes(seqs)
+    so = np.ascontiguousarray(offsets, dtype=np.uint64)
+    n = (so.size - 1) // 2
+    ed = np.zeros(max(n, 1), np.uint32)
+    mt = np.zeros((max(n, 1), 4), np.uint32)
+    tt = np.zeros((max(n, 1), 4), np.uint32)
+    rc = lib().orc_seed_match(_ptr(sb), _ptr(so), n, pattern.encode(), spaced.encode(), k, w, _ptr(ed), _ptr(mt),
+                              _ptr(tt))
+    if rc != 0:
+        raise ValueError("bad pattern, k or w")
+    return ed[:n], mt[:n], tt[:n]
 
 
 def root_loss_grad_f64(theta: np.ndarray, H: int, x: np.ndarray, y: np.ndarray):

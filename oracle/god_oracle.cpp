@@ -19,6 +19,8 @@
 //     (Sec. 3.4, Fig. 8, Sec. 3.6.3);
 //   * containment search over a database of genomes indexed on the fly in
 //     batches (Sec. 2.3);
+//   * the seed matching evaluation of Sec. 2.1.1 (Levenshtein distance and
+//     seed matching rates of four seeding algorithms on sequence pairs);
 //   * the learned-index (RMI) reference: MLP root forward/backward, leaf least
 //     squares and per-leaf error bounds in the same FP32 operation order the GPU
 //     lookup uses.
@@ -489,6 +491,72 @@ void contain(const uint8_t* db, const uint64_t* coff, uint32_t n_contigs, const 
   }
 }
 
+// ---------------------------------------------------------------- seed matching evaluation
+// Sec. 2.1.1 / 2.1.2 (Fig. 4): for a pair (S, S') of sequences, the Levenshtein
+// distance and, for four seeding algorithms, how many seeds extracted from S'
+// occur among the seeds extracted from S (the seed matching rate is matched /
+// total). Readings where the paper is silent:
+//   * Levenshtein distance with unit costs on the raw bytes;
+//   * "All Seeds": every k-mer of S (forward strand, 2k-bit code) that holds
+//     only A/C/G/T; "Minimizers": the (w,k)-minimizer keys of the
+//     unsparsified sequence (the method's double-strand minimizers with
+//     pattern 1); "Spaced": at every start i, the bases at the 1s of the
+//     spaced pattern repeated or cut to k positions (span k); "Genome-on-Diet":
+//     every k-mer of the sequence sparsified with the diet pattern at shift 0;
+//   * seeds of S' are counted with repetition; a seed matches when its code
+//     (key) is among the seeds of S.
+uint32_t levenshtein(const uint8_t* a, uint64_t m, const uint8_t* b, uint64_t n) {
+  std::vector<uint32_t> prev(n + 1), cur(n + 1);
+  for (uint64_t j = 0; j <= n; ++j) prev[j] = (uint32_t)j;
+  for (uint64_t i = 1; i <= m; ++i) {
+    cur[0] = (uint32_t)i;
+    for (uint64_t j = 1; j <= n; ++j) {
+      const uint32_t sub = prev[j - 1] + (a[i - 1] == b[j - 1] ? 0u : 1u);
+      cur[j] = std::min(std::min(prev[j] + 1, cur[j - 1] + 1), sub);
+    }
+    std::swap(prev, cur);
+  }
+  return prev[n];
+}
+
+// Codes of the seeds read at positions start + off[0..q) for every start;
+// a seed with a byte outside ACGT is skipped.
+std::vector<uint64_t> gapped_codes(const std::vector<int>& codes, const std::vector<uint64_t>& offs, uint64_t span) {
+  std::vector<uint64_t> out;
+  if (codes.size() < span) return out;
+  for (uint64_t i = 0; i + span <= codes.size(); ++i) {
+    uint64_t v = 0;
+    bool ok = true;
+    for (uint64_t o : offs) {
+      const int c = codes[i + o];
+      if (c == kN) { ok = false; break; }
+      v = v * 4 + (uint64_t)c;
+    }
+    if (ok) out.push_back(v);
+  }
+  return out;
+}
+
+void seed_sets(const uint8_t* seq, uint64_t len, const std::vector<int>& P, const std::vector<int>& SP, int k, int w,
+               std::vector<uint64_t> out[4]) {
+  std::vector<int> codes(len);
+  for (uint64_t i = 0; i < len; ++i) codes[i] = base_code(seq[i]);
+  std::vector<uint64_t> contiguous;
+  for (int i = 0; i < k; ++i) contiguous.push_back((uint64_t)i);
+  out[0] = gapped_codes(codes, contiguous, (uint64_t)k);
+  out[1].clear();
+  const std::vector<int> one{1};
+  for (const Mini& m : seq_minimizers(seq, len, one, 0, k, w)) out[1].push_back(m.key);
+  std::vector<uint64_t> spaced;
+  for (int i = 0; i < k; ++i)
+    if (SP[i % SP.size()]) spaced.push_back((uint64_t)i);
+  out[2] = gapped_codes(codes, spaced, (uint64_t)k);
+  std::vector<int> pc;
+  std::vector<uint64_t> orig;
+  sparsify(seq, len, P, 0, pc, orig);
+  out[3] = gapped_codes(pc, contiguous, (uint64_t)k);
+}
+
 // ---------------------------------------------------------------- RMI reference
 // Learned index over the sorted kept keys: a root MLP 1 -> H -> 1 (ReLU) maps the
 // normalised key to a leaf; each leaf holds a linear model of the rank. The
@@ -844,6 +912,36 @@ int orc_contain(const uint8_t* db, const uint64_t* coff, uint32_t n_contigs, con
     if (o.read_genome[r] >= 0) {
       genome_reads[o.read_genome[r]] += 1;
       genome_bases[o.read_genome[r]] += roff[r + 1] - roff[r];
+    }
+  }
+  return 0;
+}
+
+
+// Seed matching evaluation of n pairs: pair i is (seq[2i], seq[2i + 1]) with
+// CSR byte offsets (2n + 1). Per pair: ed[i]; matched[4i + a] and total[4i + a]
+// for a = All Seeds, Minimizers, Spaced, Genome-on-Diet. Returns 0, or -1 on a
+// bad pattern, k outside 1..28 or w outside 1..255.
+int orc_seed_match(const uint8_t* seqs, const uint64_t* offs, uint32_t n, const char* pattern, const char* spaced,
+                   int k, int w, uint32_t* ed, uint32_t* matched, uint32_t* total) {
+  std::vector<int> P, SP;
+  if (!parse_pattern(pattern, P) || !parse_pattern(spaced, SP) || k < 1 || k > 28 || w < 1 || w > 255) return -1;
+  for (uint32_t i = 0; i < n; ++i) {
+    const uint8_t* a = seqs + offs[2 * i];
+    const uint64_t la = offs[2 * i + 1] - offs[2 * i];
+    const uint8_t* b = seqs + offs[2 * i + 1];
+    const uint64_t lb = offs[2 * i + 2] - offs[2 * i + 1];
+    ed[i] = levenshtein(a, la, b, lb);
+    std::vector<uint64_t> sa[4], sb[4];
+    seed_sets(a, la, P, SP, k, w, sa);
+    seed_sets(b, lb, P, SP, k, w, sb);
+    for (int g = 0; g < 4; ++g) {
+      std::vector<uint64_t> set = sa[g];
+      std::sort(set.begin(), set.end());
+      uint32_t hit = 0;
+      for (uint64_t v : sb[g]) hit += std::binary_search(set.begin(), set.end(), v) ? 1u : 0u;
+      matched[4 * i + g] = hit;
+      total[4 * i + g] = (uint32_t)sb[g].size();
     }
   }
   return 0;
