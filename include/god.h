@@ -314,6 +314,27 @@ int god_contain(const uint8_t *db, const uint64_t *contig_offsets, uint32_t n_co
                 int32_t *read_genome, uint32_t *read_votes, uint64_t *genome_reads, uint64_t *genome_bases,
                 void *stream);
 
+/* ----------------------------------------------------------------- seed matching evaluation
+ * god_seed_match: the evaluation of Sec. 2.1.1 / Fig. 4 on n_pairs sequence
+ * pairs (S, S') = (sequence 2i, sequence 2i + 1) of at most 1024 bases each:
+ *   ed[i]            Levenshtein distance (unit costs, raw bytes);
+ *   matched[4i + a]  seeds extracted from S' that occur among S's seeds;
+ *   total[4i + a]    seeds extracted from S' (counted with repetition);
+ * for a = 0 All Seeds (every k-mer of A/C/G/T bases, forward code),
+ * 1 Minimizers ((w,k)-minimizer keys of the unsparsified sequence),
+ * 2 Spaced (at every start, the bases under the 1s of `spaced` repeated or
+ * cut to k positions), 3 Genome-on-Diet (every k-mer of the sequence
+ * sparsified by `pattern` at shift 0). The seed matching rate is
+ * matched / total.
+ *   seqs, offsets  host or device; offsets has 2 n_pairs + 1 entries.
+ *   ed, matched, total  host or device (all the same kind).
+ * Errors: GOD_EINVAL (bad patterns, k outside 1..28, w outside 1..255, a
+ * sequence longer than 1024 bases or decreasing offsets), GOD_ENOMEM,
+ * GOD_ECUDA. Synchronous. */
+int god_seed_match(const uint8_t *seqs, const uint64_t *offsets, uint32_t n_pairs, const char *pattern,
+                   const char *spaced, int k, int w, uint32_t *ed, uint32_t *matched, uint32_t *total,
+                   void *stream);
+
 /* ----------------------------------------------------------------- learned index
  * Gradient of the root MLP's mean squared error (1 -> H -> 1, ReLU; parameter
  * layout W1[H], b1[H], W2[H], b2) over samples (x[i], y[i]), computed by the

@@ -271,6 +271,21 @@ def god_contain(db, contig_offsets, contig_genome, n_genomes: int, reads, read_o
     return rg[:nr], rv[:nr], gr[:n_genomes], gb[:n_genomes]
 
 
+def god_seed_match(seqs, offsets, pattern: str, spaced: str, k: int, w: int, stream=None):
+    """Seed matching evaluation (god_seed_match) of host pairs: (Levenshtein
+    distance [n], matched [n, 4], total [n, 4]); columns All Seeds,
+    Minimizers, Spaced, Genome-on-Diet."""
+    seqs = _u8(seqs)
+    offs = np.ascontiguousarray(offsets, dtype=np.uint64)
+    n = (offs.size - 1) // 2
+    ed = np.zeros(max(n, 1), np.uint32)
+    mt = np.zeros((max(n, 1), 4), np.uint32)
+    tt = np.zeros((max(n, 1), 4), np.uint32)
+    check(load().god_seed_match(_ptr(seqs), _ptr(offs), n, pattern.encode(), spaced.encode(), k, w, _ptr(ed),
+                                _ptr(mt), _ptr(tt), _stream_ptr(stream)))
+    return ed[:n], mt[:n], tt[:n]
+
+
 def god_rmi_root_grad(theta, H: int, x, y):
     th = np.ascontiguousarray(theta, np.float32)
     xs = np.ascontiguousarray(x, np.float32)

@@ -20,7 +20,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libgod.so")
 INCLUDE = os.path.join(ROOT, "include")
 SOURCES = ["api.cu", "scan.cu", "sketch.cu", "radix.cu", "index.cu", "rmi.cu", "seed.cu", "serve.cu", "vote.cu",
-           "segment.cu", "contain.cu"]
+           "segment.cu", "contain.cu", "seedmatch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
               "-Xcompiler", "-Wall", "-I", INCLUDE]
@@ -138,6 +138,7 @@ SIGNATURES = {
     "god_vote": (I32, [P_, U64, P_, U32, C.POINTER(VoteParams), P_, P_, P_]),
     "god_contain_params_init": (None, [C.POINTER(ContainParams)]),
     "god_contain": (I32, [P_, P_, U32, P_, U32, P_, P_, U32, C.POINTER(ContainParams), P_, P_, P_, P_, P_]),
+    "god_seed_match": (I32, [P_, P_, U32, C.c_char_p, C.c_char_p, I32, I32, P_, P_, P_, P_]),
     "god_free": (None, [P_]),
     "god_launch_count": (U64, []),
     "god_prof_enable": (None, [I32]),

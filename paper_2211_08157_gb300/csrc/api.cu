@@ -782,6 +782,54 @@ int god_contain(const uint8_t* db, const uint64_t* contig_offsets, uint32_t n_co
                         read_votes, genome_reads, genome_bases, st);
 }
 
+int god_seed_match(const uint8_t* seqs, const uint64_t* offsets, uint32_t n_pairs, const char* pattern,
+                   const char* spaced, int k, int w, uint32_t* ed, uint32_t* matched, uint32_t* total, void* stream) {
+  PatternInfo P, SP;
+  if (parse_pattern(pattern, &P) != GOD_OK || parse_pattern(spaced, &SP) != GOD_OK || k < 1 || k > 28 || w < 1 ||
+      w > 255) {
+    set_error("god_seed_match: bad pattern, spaced pattern, k or w");
+    return GOD_EINVAL;
+  }
+  if (n_pairs == 0) return GOD_OK;
+  if (!seqs || !offsets || !ed || !matched || !total) {
+    set_error("god_seed_match: null argument");
+    return GOD_EINVAL;
+  }
+  const bool dev_out = is_device_ptr(ed);
+  if (dev_out != is_device_ptr(matched) || dev_out != is_device_ptr(total)) {
+    set_error("god_seed_match: outputs must all be device or all host memory");
+    return GOD_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const uint64_t n_off = 2 * (uint64_t)n_pairs + 1;
+  DBuf<uint8_t> hold_o, hold_s;
+  const void* doff = nullptr;
+  const void* dseq = nullptr;
+  uint64_t bytes = 0;
+  if (is_device_ptr(offsets)) {
+    doff = offsets;
+    GOD_CK(cudaMemcpyAsync(&bytes, offsets + n_off - 1, 8, cudaMemcpyDeviceToHost, st));
+    GOD_CK(cudaStreamSynchronize(st));
+  } else {
+    bytes = offsets[n_off - 1];
+    GOD_TRY(to_device(offsets, n_off * 8, hold_o, &doff, st));
+  }
+  GOD_TRY(to_device(seqs, bytes, hold_s, &dseq, st));
+  if (dev_out)
+    return seed_match_device((const uint8_t*)dseq, (const uint64_t*)doff, n_pairs, P, SP, k, w, ed, matched, total,
+                             st);
+  DBuf<uint32_t> de, dm, dt;
+  GOD_TRY(de.alloc(n_pairs, st));
+  GOD_TRY(dm.alloc(4 * (uint64_t)n_pairs, st));
+  GOD_TRY(dt.alloc(4 * (uint64_t)n_pairs, st));
+  GOD_TRY(seed_match_device((const uint8_t*)dseq, (const uint64_t*)doff, n_pairs, P, SP, k, w, de.p, dm.p, dt.p, st));
+  GOD_CK(cudaMemcpyAsync(ed, de.p, (uint64_t)n_pairs * 4, cudaMemcpyDeviceToHost, st));
+  GOD_CK(cudaMemcpyAsync(matched, dm.p, (uint64_t)n_pairs * 16, cudaMemcpyDeviceToHost, st));
+  GOD_CK(cudaMemcpyAsync(total, dt.p, (uint64_t)n_pairs * 16, cudaMemcpyDeviceToHost, st));
+  GOD_CK(cudaStreamSynchronize(st));
+  return GOD_OK;
+}
+
 int god_rmi_root_grad(const float* theta, int H, const float* x, const float* y, uint64_t n, float* grad, float* loss) {
   if (!theta || !grad || !loss || (n && (!x || !y)) || H != kRootHidden) return GOD_EINVAL;
   const int np = 3 * H + 1;

@@ -304,6 +304,10 @@ int contain_device(const uint8_t* db, bool db_on_device, const uint64_t* coff, u
                    uint32_t n_genomes, const uint8_t* d_reads, const uint64_t* d_roff, uint32_t n_reads,
                    uint64_t read_bytes, const god_contain_params& prm, int32_t* h_read_genome,
                    uint32_t* h_read_votes, uint64_t* h_genome_reads, uint64_t* h_genome_bases, cudaStream_t st);
+// Seed matching evaluation over device arrays (see god_seed_match).
+int seed_match_device(const uint8_t* d_seqs, const uint64_t* d_offs, uint32_t n, const PatternInfo& P,
+                      const PatternInfo& SP, int k, int w, uint32_t* d_ed, uint32_t* d_matched, uint32_t* d_total,
+                      cudaStream_t st);
 // Location voting over device arrays (see god_vote).
 int vote_device(const god_anchor* d_a, uint64_t m, const uint64_t* d_offs, uint32_t n, const god_vote_params& p,
                 god_vote_rec* d_out, uint32_t* d_counts, cudaStream_t st);
