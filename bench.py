@@ -419,6 +419,55 @@ def workload_line(god, torch, dev, stream, flush, name, ref=None):
     return out, ref
 
 
+# ----------------------------------------------------------------------------- seed matching evaluation
+def seed_match_line(god, torch, dev, stream, flush, n_pairs=100_000, length=1000, seed=77):
+    """The evaluation of Sec. 2.1.1 on the GPU: n_pairs 1000-base pairs, each a
+    random sequence and a copy with 0-300 substitutions at random positions;
+    Levenshtein distance and the matched / total seeds of the four seeding
+    algorithms at k = 8, w = 6, pattern 100 (spaced seeds with 100 repeated).
+    Reports pairs/s, and per algorithm the share of pairs accepted at a few
+    edit-distance thresholds (threshold rate = the smallest matching rate of
+    the pairs within the distance; accepted = pairs at or above it)."""
+    rng = np.random.default_rng(seed)
+    S = synth.ACGT[rng.integers(0, 4, (n_pairs, length))]
+    T = S.copy()
+    n_sub = rng.integers(0, 301, n_pairs)
+    for i in range(n_pairs):
+        pos = rng.choice(length, int(n_sub[i]), replace=False)
+        T[i, pos] = synth.ACGT[(np.searchsorted(synth.ACGT, T[i, pos]) + rng.integers(1, 4, pos.size)) % 4]
+    seqs = np.stack([S, T], axis=1).reshape(-1)
+    offs = np.arange(0, 2 * n_pairs * length + 1, length, dtype=np.uint64)
+    d_seqs = torch.from_numpy(seqs).to(dev)
+    d_offs = torch.from_numpy(offs.view(np.int64)).to(dev)
+    ed = torch.empty(n_pairs, dtype=torch.int32, device=dev)
+    mt = torch.empty((n_pairs, 4), dtype=torch.int32, device=dev)
+    tt = torch.empty((n_pairs, 4), dtype=torch.int32, device=dev)
+    L = god.load()
+    import ctypes as C
+
+    def run():
+        god.check(L.god_seed_match(C.c_void_p(d_seqs.data_ptr()), C.c_void_p(d_offs.data_ptr()), n_pairs, b"100",
+                                   b"100", 8, 6, C.c_void_p(ed.data_ptr()), C.c_void_p(mt.data_ptr()),
+                                   C.c_void_p(tt.data_ptr()), C.c_void_p(stream.cuda_stream)))
+
+    run()
+    ms = time_events(stream, flush, run)
+    e = ed.cpu().numpy()
+    rate = mt.cpu().numpy() / np.maximum(tt.cpu().numpy(), 1)
+    accepted = {}
+    for thr in (20, 50, 100, 138, 200, 295):
+        within = e <= thr
+        row = {}
+        for a, name in enumerate(("all", "minimizer", "spaced", "god")):
+            cut = rate[within, a].min() if within.any() else 1.0
+            row[name] = float((rate[:, a] >= cut).mean())
+        accepted[str(thr)] = row
+    return {"pairs": n_pairs, "length": length, "k": 8, "w": 6, "pattern": "100", "spaced": "100",
+            "substitutions": "uniform 0-300 per pair", "ms": ms, "pairs_per_s": n_pairs / (ms / 1e3),
+            "dp_cells_per_s": n_pairs * length * length / (ms / 1e3),
+            "accepted_share_by_edit_distance_threshold": accepted}
+
+
 # ----------------------------------------------------------------------------- GPU arm
 def main():
     ap = argparse.ArgumentParser()
@@ -432,6 +481,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the other index kind's seed-only line")
+    ap.add_argument("--no-seed-match", action="store_true", help="skip the seed matching evaluation line")
     ap.add_argument("--no-workloads", action="store_true",
                     help="skip the HiFi-like and human-scale ONT-like seeding lines")
     ap.add_argument("--serving-seconds", type=float, default=3.0, help="0 skips the serving measurement")
@@ -666,6 +716,10 @@ def main():
                     r0 = r
             workloads[wname], refs[wname] = workload_line(god, torch, dev, stream, flush, wname, r0)
 
+    seed_match = None
+    if rank == 0 and not args.no_seed_match:
+        seed_match = seed_match_line(god, torch, dev, stream, flush)
+
     serving = None
     if args.serving_seconds > 0 and rank == 0:
         swl = synth.WORKLOADS[args.serving_workload]
@@ -727,7 +781,7 @@ def main():
             "gpu_launches": int(launches),
             "roofline": roof, "sketch_roofline": sketch_roof, "kernels": kernels,
             "kernels_note": f"per-step means over {prof_steps} extra steps with every launch timed by CUDA events",
-            "seed_only_resident_index": seed_only, "index_build_resident_reference": index_build, "workloads": workloads, "serving": serving, "e2e": e2e,
+            "seed_only_resident_index": seed_only, "index_build_resident_reference": index_build, "workloads": workloads, "seed_match": seed_match, "serving": serving, "e2e": e2e,
             "cpu_baseline": cpu,
             "clocks": clk,
         }
