@@ -55,13 +55,16 @@ def sketch_ops_per_base(k: int) -> int:
     return 4 + 7 + 5 + 23 + (12 if k <= 15 else 24) + 2
 
 
+SKETCH_SOURCES = {"sketch": "sketch.cu", "sketch_seg": "sketch_seg.cu"}
+
+
 def recorded_traffic(kernel: str, workload: str):
     """Per-launch DRAM bytes (read + write) of `kernel` from the committed ncu
     summary, if it was captured on this workload and on the current kernel
     source (source hash matches), else None."""
     import hashlib
     path = os.path.join(ROOT, "profiles", f"{kernel}_traffic.json")
-    src = os.path.join(ROOT, "paper_2211_08157_gb300", "csrc", "sketch.cu")
+    src = os.path.join(ROOT, "paper_2211_08157_gb300", "csrc", SKETCH_SOURCES.get(kernel, "sketch.cu"))
     try:
         d = json.load(open(path))
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()
@@ -586,13 +589,13 @@ def main():
     tname = max(prof_all.items(), key=lambda kv: kv[1][1])[0]
     tl, tms, tbytes, tunits = prof[tname] if tname in prof else prof_all[tname]
     per_launch_s = (tms / tl) / 1e3
-    if tname == "sketch":
+    if tname in ("sketch", "sketch_seg"):
         # algorithmic bytes: 1 B per patterned base read + 16 B per minimizer
         # record written; the integer-issue view of the same launches beside it
         bpl = tbytes / tl
         achieved = bpl / per_launch_s / 1e9
         ops = sketch_ops_per_base(wl.k) * tunits / tl            # algorithmic int32 ops per launch
-        tr = recorded_traffic("sketch", wl.name)
+        tr = recorded_traffic(tname, wl.name)
         roof = {"kernel": tname, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "traffic": tr["bytes_per_launch"] if tr else None,
                 "traffic_source": tr["source"] if tr else "no capture on the current kernel source",
@@ -610,12 +613,17 @@ def main():
     else:
         roof = {"kernel": tname, "bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None,
                 "traffic": None, "peak_source": peak_src, "ms_per_launch": tms / tl}
-    sk = prof.get("sketch")
+    # both sketch kernels of a step together: the reference's (tile kernel) and
+    # the reads' (per-segment kernel when their segments are short)
+    sks = [prof[n] for n in ("sketch", "sketch_seg") if n in prof]
     sketch_roof = None
-    if sk and sk[2] > 0:
-        a = (sk[2] / sk[0]) / ((sk[1] / sk[0]) / 1e3) / 1e9
-        sketch_roof = {"hbm_achieved_gbs": a, "hbm_frac": a / hbm, "ms_per_step": sk[1] / args.steps,
-                       "patterned_bases_per_s": sk[3] / (sk[1] / 1e3)}
+    if sks and sum(x[2] for x in sks) > 0:
+        sk_ms = sum(x[1] for x in sks)
+        a = sum(x[2] for x in sks) / (sk_ms / 1e3) / 1e9
+        sketch_roof = {"hbm_achieved_gbs": a, "hbm_frac": a / hbm, "ms_per_step": sk_ms / args.steps,
+                       "patterned_bases_per_s": sum(x[3] for x in sks) / (sk_ms / 1e3),
+                       "per_kernel_ms_per_step": {n: prof[n][1] / args.steps for n in ("sketch", "sketch_seg")
+                                                  if n in prof}}
     kernels = {k: {"launches_per_step": v[0] / prof_steps, "ms_per_step": v[1] / prof_steps,
                    "share": v[1] / sum(x[1] for x in prof_all.values())} for k, v in
                sorted(prof_all.items(), key=lambda kv: -kv[1][1])}

@@ -354,8 +354,8 @@ void god_free(void *p);
 uint64_t god_launch_count(void);
 
 /* Opt-in kernel timing: while enabled (on = 1), every launch is bracketed by a
- * pair of CUDA events on its stream; on = 2 times only the sketch kernel's
- * launches (two events per launch, so the rest of a timed step runs as
+ * pair of CUDA events on its stream; on = 2 times only the sketch kernels'
+ * launches ("sketch": the tile kernel; "sketch_seg": one thread per segment) (two events per launch, so the rest of a timed step runs as
  * without timing); 0 switches timing off. god_prof_report writes a JSON object
  * {"kernel": [launches, total_ms, algorithmic_bytes, units], ...} (bytes and
  * units are filled in for the sketch kernel: patterned bases read plus 16-byte

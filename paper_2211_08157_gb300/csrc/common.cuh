@@ -30,14 +30,19 @@ int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
 extern std::atomic<uint64_t> g_launches;
 extern std::atomic<int> g_prof_on;
 // Opt-in per-kernel timing: an event pair around each launch, resolved later.
-// Mode 1 times every launch, mode 2 only the sketch kernel's.
+// Mode 1 times every launch, mode 2 only the sketch kernels' ("sketch", the
+// tile kernel, and "sketch_seg", the per-segment kernel).
 inline bool prof_wants(const char* kernel) {
   const int m = g_prof_on.load(std::memory_order_relaxed);
   if (m == 1) return true;
   if (m != 2) return false;
   const char* s = "sketch";
   while (*s && *kernel == *s) ++s, ++kernel;
-  return *s == 0 && *kernel == 0;
+  if (*s) return false;
+  if (*kernel == 0) return true;
+  const char* t = "_seg";
+  while (*t && *kernel == *t) ++t, ++kernel;
+  return *t == 0 && *kernel == 0;
 }
 void prof_begin(cudaStream_t st, cudaEvent_t* a);
 void prof_end(const char* name, cudaStream_t st, cudaEvent_t a);
@@ -154,6 +159,8 @@ struct SketchJob {
   uint32_t* seg_cnt;          // optional per-segment minimizer counts (zeroed by caller)
   uint32_t* read_flag;        // optional: set to 1 for reads with an N in a capped segment
   int tune;                   // 1: pick the launch shape with the autotuner (cached per shape class)
+  uint32_t max_m;             // longest segment's m when known (0 = unknown); batches of short
+                              // segments then run the one-thread-per-segment kernel
 };
 
 // Runs the fused sparsify + 2-bit code + hash + window-minimum kernel over the
@@ -172,8 +179,16 @@ struct StagedSketch {
   DBuf<uint64_t> sub_off;
   uint64_t n_sub = 0, total = 0;
   int WT = 0;
+  // when set, sub-tile s's records start at staging[sub_base[s]] instead of
+  // staging[s * WT] (the per-segment kernel: one sub-tile per segment, based
+  // at the segment's virtual offset)
+  const uint64_t* sub_base = nullptr;
 };
 int run_sketch_staged(const SketchJob& job, cudaStream_t st, StagedSketch& out, const SketchTune* tune);
+// The one-thread-per-segment kernel (sketch_seg.cu): whether it takes this
+// job, and the pass itself (same records and order as the tile kernel).
+bool sketch_segments_ok(const SketchJob& job);
+int run_sketch_segments(const SketchJob& job, cudaStream_t st, StagedSketch& out);
 SketchTune default_sketch_tune(int k, int w);
 
 // ------------------------------------------------------------------ scan

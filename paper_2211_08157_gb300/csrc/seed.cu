@@ -72,7 +72,9 @@ __device__ __forceinline__ void warp_append(bool f, uint32_t i, uint32_t* list, 
 }
 
 __global__ void make_pa_segments(const uint64_t* __restrict__ offs, uint32_t n, PatternInfo P, uint32_t cap,
-                                 SegDesc* __restrict__ segs, uint32_t* __restrict__ vlen, int* err) {
+                                 SegDesc* __restrict__ segs, uint32_t* __restrict__ vlen, int* err,
+                                 uint32_t* max_m) {
+  uint32_t mlen = 0;
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t b = offs[i];
     uint64_t e = offs[i + 1];
@@ -87,15 +89,20 @@ __global__ void make_pa_segments(const uint64_t* __restrict__ offs, uint32_t n, 
       const uint32_t mm = (uint32_t)std::min<uint64_t>(m, cap);
       segs[g] = SegDesc{b, mm, (uint32_t)i, (uint32_t)s, m > cap ? kSegCapped : 0u};
       vlen[g] = mm + 1;
+      mlen = mm > mlen ? mm : mlen;
     }
   }
+  const unsigned am = __activemask();
+  mlen = __reduce_max_sync(am, mlen);
+  if ((int)(threadIdx.x & 31) == __ffs(am) - 1) atomicMax(max_m, mlen);
 }
 
 // Segments at full length for listed reads: all shifts (fallback PA) or the
 // chosen shift only (seeding pass).
 __global__ void make_list_segments(const uint64_t* __restrict__ offs, const uint32_t* __restrict__ list, uint32_t nl,
                                    PatternInfo P, int all_shifts, const uint32_t* __restrict__ shift,
-                                   SegDesc* __restrict__ segs, uint32_t* __restrict__ vlen) {
+                                   SegDesc* __restrict__ segs, uint32_t* __restrict__ vlen, uint32_t* max_m) {
+  uint32_t mlen = 0;
   for (uint64_t li = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; li < nl; li += (uint64_t)gridDim.x * blockDim.x) {
     const uint32_t i = list[li];
     const uint64_t b = offs[i], len = offs[i + 1] - b;
@@ -104,14 +111,19 @@ __global__ void make_list_segments(const uint64_t* __restrict__ offs, const uint
         const uint64_t m = patterned_len(P, len, s);
         segs[li * P.p + s] = SegDesc{b, (uint32_t)m, i, (uint32_t)s, 0u};
         vlen[li * P.p + s] = (uint32_t)m + 1;
+        mlen = (uint32_t)m > mlen ? (uint32_t)m : mlen;
       }
     } else {
       const uint32_t s = shift[i];
       const uint64_t m = patterned_len(P, len, s);
       segs[li] = SegDesc{b, (uint32_t)m, i, s, 0u};
       vlen[li] = (uint32_t)m + 1;
+      mlen = (uint32_t)m > mlen ? (uint32_t)m : mlen;
     }
   }
+  const unsigned am = __activemask();
+  mlen = __reduce_max_sync(am, mlen);
+  if ((int)(threadIdx.x & 31) == __ffs(am) - 1) atomicMax(max_m, mlen);
 }
 
 // Sum of index counts over a segment's first t records (t = 0: all) and over
@@ -629,9 +641,56 @@ __global__ void __launch_bounds__(kLargeThreads) fill_sort_large(RecSets sets, c
   }
 }
 
-// Staged sketch output -> ordered per-record (position << 1 | z) words and
-// index lookups (warp per sketch sub-tile; a lookup result is start | count
-// << 32). The key is not kept: nothing after the lookup needs it.
+// Looks up U records (rp[u] valid when ok[u]) and writes (read position << 1
+// | z) and the lookup result (start | count << 32) to pz / sc at oi[u].
+template <int VIA, int U>
+__device__ __forceinline__ void lookup_records(const RmiRoot& R, const DeviceIndex& di, const MinRec* const (&rp)[U],
+                                               const bool (&ok)[U], const uint64_t (&oi)[U],
+                                               uint32_t* __restrict__ pz, uint64_t* __restrict__ sc) {
+  uint64_t key[U], rk[U];
+  uint32_t pzv[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    uint4 r = make_uint4(0, 0, 0, 0);
+    if (ok[u]) r = __ldcs(reinterpret_cast<const uint4*>(rp[u]));   // read once
+    key[u] = ((uint64_t)r.y << 32) | r.x;
+    pzv[u] = (r.z << 1) | (r.w & 1u);
+  }
+  uint64_t pay[U];
+  if (VIA == 1) {
+    RmiLeaf L[U];
+    bool hashed[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      hashed[u] = !rmi_in_range(R, key[u]);
+      L[u] = ok[u] && !hashed[u] ? di.leaves[rmi_root_leaf(R, key[u])] : RmiLeaf{0, 0.0f, 0.0f};
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      hashed[u] = hashed[u] || (uint32_t)(L[u].base_eps >> 56) > di.eps_max;
+      pay[u] = !ok[u] ? 0 : hashed[u] ? ht_find(di, key[u]) : rank_payload(di, rmi_rank_in_leaf(di, L[u], key[u]));
+    }
+  } else {
+    uint64_t w[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) w[u] = ok[u] ? ht_home_word(di, key[u]) : kEmptyKey;
+#pragma unroll
+    for (int u = 0; u < U; ++u) rk[u] = ok[u] ? ht_field(di, key[u], w[u]) : kNoRank;
+#pragma unroll
+    for (int u = 0; u < U; ++u) pay[u] = field_payload(di, rk[u]);
+  }
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    if (ok[u]) {
+      pz[oi[u]] = pzv[u];
+      sc[oi[u]] = pay[u];
+    }
+  }
+}
+
+// Staged sketch output (tile kernel: WT slots per warp sub-tile) -> ordered
+// per-record (position << 1 | z) words and index lookups, a warp per
+// sub-tile. The key is not kept: nothing after the lookup needs it.
 template <int VIA>
 __global__ void __launch_bounds__(kT) compact_lookup(const MinRec* __restrict__ staging,
                                                      const uint32_t* __restrict__ sub_cnt,
@@ -653,48 +712,73 @@ __global__ void __launch_bounds__(kT) compact_lookup(const MinRec* __restrict__ 
     // flight per lane measured slower)
     constexpr int U = 2;
     for (uint32_t i0 = lane; i0 < c; i0 += 32 * U) {
-      uint64_t key[U], rk[U];
-      uint32_t pzv[U];
+      const MinRec* rp[U];
       bool ok[U];
+      uint64_t oi[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const uint32_t i = i0 + 32 * u;
         ok[u] = i < c;
-        uint4 r = make_uint4(0, 0, 0, 0);
-        if (ok[u]) r = __ldcs(reinterpret_cast<const uint4*>(src + i));   // read once
-        key[u] = ((uint64_t)r.y << 32) | r.x;
-        pzv[u] = (r.z << 1) | (r.w & 1u);
+        rp[u] = src + i;
+        oi[u] = o + i;
       }
-      uint64_t pay[U];
-      if (VIA == 1) {
-        RmiLeaf L[U];
-        bool hashed[U];
+      lookup_records<VIA, U>(R, di, rp, ok, oi, pz, sc);
+    }
+  }
+}
+
+// The same for the per-segment kernel's staging (segment s's records at
+// staging[base[s]]): a warp takes 32 consecutive segments and spreads their
+// records over its lanes; a lane finds the segment of its record by a binary
+// search over the segments' exclusive counts held one per lane.
+template <int VIA>
+__global__ void __launch_bounds__(kT) compact_lookup_seg(const MinRec* __restrict__ staging,
+                                                         const uint32_t* __restrict__ sub_cnt,
+                                                         const uint64_t* __restrict__ sub_off, uint64_t n_sub,
+                                                         const uint64_t* __restrict__ base, DeviceIndex di,
+                                                         uint32_t* __restrict__ pz, uint64_t* __restrict__ sc) {
+  __shared__ RmiRoot R;
+  if (VIA == 1) {
+    if (threadIdx.x == 0) R = *di.root;
+    __syncthreads();
+  }
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x / 32);
+  for (uint64_t grp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) / 32; grp * 32 < n_sub; grp += warps) {
+    const uint64_t s = grp * 32 + lane;
+    const uint32_t c = s < n_sub ? sub_cnt[s] : 0u;
+    const uint64_t b = s < n_sub ? base[s] : 0;
+    uint32_t inc = c;
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-          hashed[u] = !rmi_in_range(R, key[u]);
-          L[u] = ok[u] && !hashed[u] ? di.leaves[rmi_root_leaf(R, key[u])] : RmiLeaf{0, 0.0f, 0.0f};
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          hashed[u] = hashed[u] || (uint32_t)(L[u].base_eps >> 56) > di.eps_max;
-          pay[u] = !ok[u] ? 0 : hashed[u] ? ht_find(di, key[u]) : rank_payload(di, rmi_rank_in_leaf(di, L[u], key[u]));
-        }
-      } else {
-        uint64_t w[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) w[u] = ok[u] ? ht_home_word(di, key[u]) : kEmptyKey;
-#pragma unroll
-        for (int u = 0; u < U; ++u) rk[u] = ok[u] ? ht_field(di, key[u], w[u]) : kNoRank;
-#pragma unroll
-        for (int u = 0; u < U; ++u) pay[u] = field_payload(di, rk[u]);
-      }
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t y = __shfl_up_sync(FULL, inc, d);
+      if (lane >= d) inc += y;
+    }
+    const uint32_t ex = inc - c;
+    const uint32_t tot = __shfl_sync(FULL, inc, 31);
+    const uint64_t o0 = sub_off[grp * 32];
+    constexpr int U = 2;
+    for (uint32_t i0 = lane; i0 < tot; i0 += 32 * U) {
+      const MinRec* rp[U];
+      bool ok[U];
+      uint64_t oi[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        if (ok[u]) {
-          pz[o + i0 + 32 * u] = pzv[u];
-          sc[o + i0 + 32 * u] = pay[u];
+        const uint32_t i = i0 + 32 * u;
+        ok[u] = i < tot;
+        int L = 0;   // last lane whose segment starts at or before record i
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+          const uint32_t e = __shfl_sync(FULL, ex, L + step);
+          if (e <= i) L += step;
         }
+        const uint32_t eL = __shfl_sync(FULL, ex, L);
+        const uint64_t bL = __shfl_sync(FULL, b, L);
+        rp[u] = staging + bL + (i - eL);
+        oi[u] = o0 + i;
       }
+      lookup_records<VIA, U>(R, di, rp, ok, oi, pz, sc);
     }
   }
 }
@@ -708,6 +792,7 @@ struct SetBufs {
   DBuf<uint64_t> sc;
   DBuf<uint32_t> seg_cnt;
   DBuf<uint64_t> seg_off;
+  DBuf<uint32_t> max_m;      // longest segment (set by the segment builders)
   uint64_t n_seg = 0, n_rec = 0;
   RecSet view() const { return RecSet{pz.p, sc.p, seg_off.p, seg_cnt.p}; }
 };
@@ -720,8 +805,10 @@ int sketch_and_lookup(const god_index* idx, const uint8_t* d_reads, SetBufs& B, 
   GOD_TRY(exclusive_scan_u32(B.vlen.p, B.voff.p, B.n_seg, st));
   uint64_t V = 0;
   int herr = 0;
+  uint32_t max_m = 0;
   GOD_CK(cudaMemcpyAsync(&V, B.voff.p + B.n_seg, 8, cudaMemcpyDeviceToHost, st));
   if (err) GOD_CK(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  if (B.max_m.p) GOD_CK(cudaMemcpyAsync(&max_m, B.max_m.p, 4, cudaMemcpyDeviceToHost, st));
   GOD_CK(cudaStreamSynchronize(st));
   if (herr) {
     set_error("seed: offsets must be non-decreasing and each read < 2^31 bytes");
@@ -741,6 +828,7 @@ int sketch_and_lookup(const god_index* idx, const uint8_t* d_reads, SetBufs& B, 
   job.seg_cnt = B.seg_cnt.p;
   job.read_flag = read_flag;
   job.tune = idx->params.tune;
+  job.max_m = max_m;
   StagedSketch SS;
   GOD_TRY(run_sketch_staged(job, st, SS, nullptr));
   B.n_rec = SS.total;
@@ -748,17 +836,31 @@ int sketch_and_lookup(const god_index* idx, const uint8_t* d_reads, SetBufs& B, 
   GOD_TRY(B.sc.alloc(SS.total, st));
   if (SS.total) {
     const DeviceIndex di = device_view(idx, via);
-    const unsigned blocks = (unsigned)std::min<uint64_t>((SS.n_sub * 32 + kT - 1) / kT, (uint64_t)num_sms() * 16);
-    if (via == 1 && di.leaves)
-      GOD_LAUNCH(compact_lookup<1>, blocks, kT, 0, st, SS.staging.p, SS.sub_cnt.p, SS.sub_off.p, SS.n_sub, SS.WT,
-                 di, B.pz.p, B.sc.p);
-    else
-      GOD_LAUNCH(compact_lookup<0>, blocks, kT, 0, st, SS.staging.p, SS.sub_cnt.p, SS.sub_off.p, SS.n_sub, SS.WT,
-                 di, B.pz.p, B.sc.p);
+    const bool learned = via == 1 && di.leaves;
+    if (SS.sub_base) {
+      const unsigned blocks =
+          (unsigned)std::min<uint64_t>(((SS.n_sub + 31) / 32 * 32 + kT - 1) / kT, (uint64_t)num_sms() * 16);
+      if (learned)
+        GOD_LAUNCH(compact_lookup_seg<1>, blocks, kT, 0, st, SS.staging.p, SS.sub_cnt.p, SS.sub_off.p, SS.n_sub,
+                   SS.sub_base, di, B.pz.p, B.sc.p);
+      else
+        GOD_LAUNCH(compact_lookup_seg<0>, blocks, kT, 0, st, SS.staging.p, SS.sub_cnt.p, SS.sub_off.p, SS.n_sub,
+                   SS.sub_base, di, B.pz.p, B.sc.p);
+    } else {
+      const unsigned blocks =
+          (unsigned)std::min<uint64_t>((SS.n_sub * 32 + kT - 1) / kT, (uint64_t)num_sms() * 16);
+      if (learned)
+        GOD_LAUNCH(compact_lookup<1>, blocks, kT, 0, st, SS.staging.p, SS.sub_cnt.p, SS.sub_off.p, SS.n_sub, SS.WT,
+                   di, B.pz.p, B.sc.p);
+      else
+        GOD_LAUNCH(compact_lookup<0>, blocks, kT, 0, st, SS.staging.p, SS.sub_cnt.p, SS.sub_off.p, SS.n_sub, SS.WT,
+                   di, B.pz.p, B.sc.p);
+    }
     // algorithmic bytes: record read 16, position word 4, result 8, one table
     // slot 8 and the key's two offsets 8
-    prof_add_work(via == 1 && di.leaves ? "compact_lookup<1>" : "compact_lookup<0>", 44.0 * (double)SS.total,
-                  (double)SS.total);
+    prof_add_work(SS.sub_base ? (learned ? "compact_lookup_seg<1>" : "compact_lookup_seg<0>")
+                              : (learned ? "compact_lookup<1>" : "compact_lookup<0>"),
+                  44.0 * (double)SS.total, (double)SS.total);
   }
   GOD_TRY(B.seg_off.alloc(B.n_seg + 1, st));
   GOD_TRY(exclusive_scan_u32(B.seg_cnt.p, B.seg_off.p, B.n_seg, st));
@@ -817,7 +919,9 @@ int seed_device(const god_index* idx, const uint8_t* d_reads, const uint64_t* d_
   PA.n_seg = (uint64_t)n * p;
   GOD_TRY(PA.segs.alloc(PA.n_seg, st));
   GOD_TRY(PA.vlen.alloc(PA.n_seg, st));
-  GOD_LAUNCH(make_pa_segments, grid_for(n), kT, 0, st, d_offs, n, P, cap, PA.segs.p, PA.vlen.p, err);
+  GOD_TRY(PA.max_m.alloc(1, st));
+  GOD_CK(cudaMemsetAsync(PA.max_m.p, 0, 4, st));
+  GOD_LAUNCH(make_pa_segments, grid_for(n), kT, 0, st, d_offs, n, P, cap, PA.segs.p, PA.vlen.p, err, PA.max_m.p);
   GOD_TRY(sketch_and_lookup(idx, d_reads, PA, need_full.p, via, err, st));
   GOD_LAUNCH(pa_select, grid_for(n), kT, 0, st, n, p, t, PA.segs.p, PA.view(), need_full.p, shift.p, src.p,
              seed_seg.p, read_cnt.p, fb_list.p, p2_list.p, pa_counts);
@@ -835,8 +939,10 @@ int seed_device(const god_index* idx, const uint8_t* d_reads, const uint64_t* d_
     FB.n_seg = n_fb * p;
     GOD_TRY(FB.segs.alloc(FB.n_seg, st));
     GOD_TRY(FB.vlen.alloc(FB.n_seg, st));
+    GOD_TRY(FB.max_m.alloc(1, st));
+    GOD_CK(cudaMemsetAsync(FB.max_m.p, 0, 4, st));
     GOD_LAUNCH(make_list_segments, grid_for(n_fb), kT, 0, st, d_offs, fb_list.p, (uint32_t)n_fb, P, 1, shift.p,
-               FB.segs.p, FB.vlen.p);
+               FB.segs.p, FB.vlen.p, FB.max_m.p);
     GOD_TRY(sketch_and_lookup(idx, d_reads, FB, nullptr, via, nullptr, st));
     GOD_LAUNCH(pa_select_list, grid_for(n_fb), kT, 0, st, fb_list.p, (uint32_t)n_fb, p, t, FB.view(), shift.p,
                seed_seg.p, read_cnt.p);
@@ -847,8 +953,10 @@ int seed_device(const god_index* idx, const uint8_t* d_reads, const uint64_t* d_
     P2.n_seg = n_p2;
     GOD_TRY(P2.segs.alloc(P2.n_seg, st));
     GOD_TRY(P2.vlen.alloc(P2.n_seg, st));
+    GOD_TRY(P2.max_m.alloc(1, st));
+    GOD_CK(cudaMemsetAsync(P2.max_m.p, 0, 4, st));
     GOD_LAUNCH(make_list_segments, grid_for(n_p2), kT, 0, st, d_offs, p2_list.p, (uint32_t)n_p2, P, 0, shift.p,
-               P2.segs.p, P2.vlen.p);
+               P2.segs.p, P2.vlen.p, P2.max_m.p);
     GOD_TRY(sketch_and_lookup(idx, d_reads, P2, nullptr, via, nullptr, st));
     GOD_LAUNCH(set_seed_seg_list, grid_for(n_p2), kT, 0, st, p2_list.p, (uint32_t)n_p2, seed_seg.p);
     GOD_LAUNCH(count_anchors_list, grid_for(n_p2 * 32), kT, 0, st, p2_list.p, (uint32_t)n_p2, P2.view(),

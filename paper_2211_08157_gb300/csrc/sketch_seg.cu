@@ -1,0 +1,208 @@
+// Seed extraction with one thread per short segment (the same minimizers as
+// the tile kernel in sketch.cu, for batches whose patterned sequences are all
+// short: short reads at every shift, the capped pattern-alignment prefixes of
+// long reads).
+//
+// A thread walks its segment (one read at one shift) base by base:
+//  * the kept base of patterned index j is read in place (orig = s + p (j / x)
+//    + off[j mod x], stepped incrementally), coded in 2 bits, and rolled into
+//    the forward and reverse-complement k-mer codes; a run counter of bases
+//    since the last N tells whether the k-mer is usable;
+//  * the canonical code is hashed -> key + 1 (0 marks a k-mer with N, all ones
+//    a palindrome, which is never chosen), as in the tile kernel;
+//  * window minima L[j] = min(key[j - w + 1 .. j]) and the largest covering
+//    minimum Y[j] = max(L[j - w + 1 .. j]) come from van Herk / Gil-Werman
+//    blocks of w k-mers: the suffix extrema of the previous block are kept in
+//    registers (the block loop is unrolled w times, so their indices are
+//    constants), the current block's keys and minima in a per-thread
+//    shared-memory row, and the running prefix extrema in registers;
+//  * k-mer u = j - w + 1 is a minimizer iff it is usable and key[u] = Y[j]
+//    (every window holding u has a minimum <= key[u]; u is some window's
+//    minimum exactly when the largest of those minima equals key[u]); keys
+//    outside the segment are 0, so windows that leave it never decide.
+// Records go, in order, to the segment's own slots of the staging array (its
+// virtual offset: m + 1 slots >= its k-mers), with the segment's count.
+#include <algorithm>
+
+#include "common.cuh"
+#include "sketch_common.cuh"
+
+namespace god {
+namespace {
+
+constexpr int kSegThreads = 128;
+constexpr uint32_t kSegMaxM = 2048;   // longest segment taken by this kernel
+
+struct SegArgs {
+  SketchJob job;
+  MinRec* staging;
+  uint32_t* sub_cnt;
+};
+
+template <typename KT, int HM, int W>
+__global__ void __launch_bounds__(kSegThreads) sketch_seg_kernel(const __grid_constant__ SegArgs a) {
+  extern __shared__ __align__(16) unsigned char seg_smem[];
+  constexpr int ROW = 2 * W + 1;              // keys B[W], minima C[W]; odd stride: no bank conflicts
+  __shared__ uint8_t s_lut[256];
+  __shared__ uint32_t s_off[kMaxPattern], s_delta[kMaxPattern];
+  const SketchJob& J = a.job;
+  const int p = J.pat.p, x = J.pat.x, k = J.k;
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) s_lut[i] = (uint8_t)base_code((uint8_t)i);
+  for (int i = threadIdx.x; i < x; i += blockDim.x) {
+    s_off[i] = (uint32_t)J.pat.off[i];
+    s_delta[i] = (uint32_t)(i + 1 < x ? J.pat.off[i + 1] - J.pat.off[i] : p + J.pat.off[0] - J.pat.off[i]);
+  }
+  __syncthreads();
+  KT* B = reinterpret_cast<KT*>(seg_smem) + threadIdx.x * ROW;
+  KT* C = B + W;
+  const uint64_t mask = (k >= 32) ? ~0ULL : ((1ULL << (2 * k)) - 1);
+  const uint32_t rshift = 2 * k - 2;
+  const uint32_t xinv = 0xFFFFFFFFu / (uint32_t)x;
+  const KT PALIN = (KT)~(KT)0;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < J.n_seg; g += stride) {
+    const SegDesc d = J.segs[g];
+    const uint32_t m = d.m;
+    const uint8_t* src = J.bytes + d.byte_off + d.shift;
+    const uint32_t nk = m >= (uint32_t)k ? m - k + 1 : 0;
+    MinRec* out = a.staging + J.seg_voff[g];
+    uint32_t cnt = 0;
+    uint64_t fwd = 0, rev = 0;
+    uint32_t run = 0, nflag = 0;
+    uint32_t o = s_off[0], r = 0;               // original offset and phase of the next base
+    // bases of the first k - 1 positions
+    const uint32_t pre = min(m, (uint32_t)k - 1);
+    for (uint32_t i = 0; i < pre; ++i) {
+      const uint32_t c = s_lut[__ldg(src + o)];
+      o += s_delta[r];
+      r = r + 1 == (uint32_t)x ? 0 : r + 1;
+      nflag |= c >> 2;
+      run = c > 3 ? 0 : run + 1;
+      fwd = (fwd << 2) | (c & 3u);
+      rev = (rev >> 2) | ((uint64_t)(3u - (c & 3u)) << rshift);
+    }
+    KT A[W + 1], D[W + 1];                      // suffix minima / maxima of the previous block
+#pragma unroll
+    for (int t = 0; t <= W; ++t) {
+      A[t] = 0;                                 // k-mers before the segment read as 0
+      D[t] = 0;
+    }
+    KT pm = 0, px = 0;
+    uint32_t zr = 0;                            // strand bits of the last 32 k-mers (bit 0 = newest)
+    const uint32_t steps = nk ? nk + W - 1 : 0;
+    for (uint32_t j0 = 0; j0 < steps; j0 += W) {
+#pragma unroll
+      for (int t = 0; t < W; ++t) {
+        const uint32_t j = j0 + t;
+        KT key = 0;
+        uint32_t z = 0;
+        if (j < nk) {
+          const uint32_t c = s_lut[__ldg(src + o)];
+          o += s_delta[r];
+          r = r + 1 == (uint32_t)x ? 0 : r + 1;
+          nflag |= c >> 2;
+          run = c > 3 ? 0 : run + 1;
+          fwd = ((fwd << 2) | (c & 3u)) & mask;
+          rev = (rev >> 2) | ((uint64_t)(3u - (c & 3u)) << rshift);
+          if (run >= (uint32_t)k) {
+            if (!(k & 1) && fwd == rev) {
+              key = PALIN;
+            } else {
+              z = rev < fwd ? 1u : 0u;
+              key = (KT)(wang_mix<HM>(z ? rev : fwd, mask) + 1);
+            }
+          }
+        }
+        zr = (zr << 1) | z;
+        B[t] = key;
+        pm = t == 0 ? key : min(pm, key);
+        const KT L = t == W - 1 ? pm : min(A[t + 1], pm);
+        C[t] = L;
+        px = t == 0 ? L : max(px, L);
+        const KT Y = t == W - 1 ? px : max(D[t + 1], px);
+        if (j >= (uint32_t)W - 1) {
+          const KT ku = B[t + 1 < W ? t + 1 : 0];   // key of k-mer u = j - W + 1
+          if (ku == Y && ku != 0 && ku != PALIN) {
+            const uint32_t u = j - (W - 1);
+            uint32_t q, rr;
+            divmod_x(u, (uint32_t)x, xinv, q, rr);
+            MinRec rec;
+            rec.key = (uint64_t)ku - 1;
+            rec.pos = d.shift + (uint32_t)p * q + s_off[rr];
+            rec.segz = ((uint32_t)g << 1) | ((zr >> (W - 1)) & 1u);
+            out[cnt++] = rec;
+          }
+        }
+      }
+      // this block's suffix extrema for the next block
+      A[W - 1] = B[W - 1];
+      D[W - 1] = C[W - 1];
+#pragma unroll
+      for (int t = W - 2; t >= 0; --t) {
+        A[t] = min(B[t], A[t + 1]);
+        D[t] = max(C[t], D[t + 1]);
+      }
+    }
+    a.sub_cnt[g] = cnt;
+    if (J.seg_cnt) J.seg_cnt[g] = cnt;
+    if (nflag && (d.flags & kSegCapped) && J.read_flag) J.read_flag[d.read] = 1u;
+  }
+}
+
+template <typename KT, int HM, int W>
+int launch_seg(const SegArgs& a, cudaStream_t st) {
+  auto sketch_seg = sketch_seg_kernel<KT, HM, W>;
+  const size_t smem = (size_t)kSegThreads * (2 * W + 1) * sizeof(KT);
+  GOD_CK(cudaFuncSetAttribute(sketch_seg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  GOD_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sketch_seg, kSegThreads, smem));
+  per_sm = std::max(per_sm, 1);
+  const uint64_t need = (a.job.n_seg + kSegThreads - 1) / kSegThreads;
+  const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(need, (uint64_t)num_sms() * per_sm));
+  GOD_LAUNCH(sketch_seg, grid, kSegThreads, smem, st, a);
+  return GOD_OK;
+}
+
+template <int W>
+int launch_seg_w(const SegArgs& a, cudaStream_t st) {
+  const int k = a.job.k;
+  if (2 * k <= 30) return launch_seg<uint32_t, 0, W>(a, st);
+  if (2 * k <= 32) return launch_seg<uint64_t, 0, W>(a, st);
+  if (2 * k <= 46) return launch_seg<uint64_t, 1, W>(a, st);
+  return launch_seg<uint64_t, 2, W>(a, st);
+}
+
+}  // namespace
+
+bool sketch_segments_ok(const SketchJob& job) {
+  return job.max_m > 0 && job.max_m <= kSegMaxM && job.n_seg >= 1024 &&
+         (job.w == 10 || job.w == 11 || job.w == 19);
+}
+
+int run_sketch_segments(const SketchJob& job, cudaStream_t st, StagedSketch& o) {
+  o.total = 0;
+  o.n_sub = job.n_seg;
+  o.WT = 0;
+  o.sub_base = job.seg_voff;
+  GOD_TRY(o.staging.alloc(job.V, st));
+  GOD_TRY(o.sub_cnt.alloc(job.n_seg, st));
+  GOD_TRY(o.sub_off.alloc((uint64_t)job.n_seg + 1, st));
+  SegArgs a;
+  a.job = job;
+  a.staging = o.staging.p;
+  a.sub_cnt = o.sub_cnt.p;
+  if (job.w == 10) GOD_TRY(launch_seg_w<10>(a, st));
+  else if (job.w == 11) GOD_TRY(launch_seg_w<11>(a, st));
+  else GOD_TRY(launch_seg_w<19>(a, st));
+  GOD_TRY(exclusive_scan_u32(o.sub_cnt.p, o.sub_off.p, job.n_seg, st));
+  uint64_t tot = 0;
+  GOD_CK(cudaMemcpyAsync(&tot, o.sub_off.p + job.n_seg, 8, cudaMemcpyDeviceToHost, st));
+  GOD_CK(cudaStreamSynchronize(st));
+  GOD_TRY(scan_total_ok(tot, "sketch"));
+  o.total = tot;
+  // algorithmic bytes: every patterned base read once, every record written once
+  prof_add_work("sketch_seg", (double)(job.V - job.n_seg) + 16.0 * (double)tot, (double)(job.V - job.n_seg));
+  return GOD_OK;
+}
+
+}  // namespace god
