@@ -759,13 +759,14 @@ __global__ void __launch_bounds__(kT) compact_lookup_seg(const MinRec* __restric
     const uint32_t tot = __shfl_sync(FULL, inc, 31);
     const uint64_t o0 = sub_off[grp * 32];
     constexpr int U = 2;
-    for (uint32_t i0 = lane; i0 < tot; i0 += 32 * U) {
+    // warp-uniform trip count: every lane takes part in the shuffles
+    for (uint32_t b0 = 0; b0 < tot; b0 += 32 * U) {
       const MinRec* rp[U];
       bool ok[U];
       uint64_t oi[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        const uint32_t i = i0 + 32 * u;
+        const uint32_t i = b0 + lane + 32 * u;
         ok[u] = i < tot;
         int L = 0;   // last lane whose segment starts at or before record i
 #pragma unroll
