@@ -3,9 +3,12 @@
 // short: short reads at every shift, the capped pattern-alignment prefixes of
 // long reads).
 //
-// A thread walks its segment (one read at one shift) base by base:
-//  * the kept base of patterned index j is read in place (orig = s + p (j / x)
-//    + off[j mod x], stepped incrementally), coded in 2 bits, and rolled into
+// A warp takes 32 consecutive segments, one per lane. Their bytes (for short
+// reads one contiguous span) are loaded by the whole warp with coalesced
+// loads, coded in 2 bits on the way, into shared memory; a span past 4 KB is
+// read in place instead. Then each thread walks its segment base by base:
+//  * the kept base of patterned index j (orig = s + p (j / x) + off[j mod x],
+//    stepped incrementally) is taken in its 2-bit code and rolled into
 //    the forward and reverse-complement k-mer codes; a run counter of bases
 //    since the last N tells whether the k-mer is usable;
 //  * the canonical code is hashed -> key + 1 (0 marks a k-mer with N, all ones
@@ -32,6 +35,7 @@ namespace {
 
 constexpr int kSegThreads = 128;
 constexpr uint32_t kSegMaxM = 2048;   // longest segment taken by this kernel
+constexpr int kWarpBytes = 4096;      // bytes a warp stages for its 32 segments
 
 struct SegArgs {
   SketchJob job;
@@ -43,8 +47,11 @@ template <typename KT, int HM, int W>
 __global__ void __launch_bounds__(kSegThreads) sketch_seg_kernel(const __grid_constant__ SegArgs a) {
   extern __shared__ __align__(16) unsigned char seg_smem[];
   constexpr int ROW = 2 * W + 1;              // keys B[W], minima C[W]; odd stride: no bank conflicts
+  constexpr int WARPS = kSegThreads / 32;
+  const unsigned FULL = 0xffffffffu;
   __shared__ uint8_t s_lut[256];
   __shared__ uint32_t s_off[kMaxPattern], s_delta[kMaxPattern];
+  __shared__ uint8_t s_codes[WARPS][kWarpBytes];   // the warp's bytes, already 2-bit coded
   const SketchJob& J = a.job;
   const int p = J.pat.p, x = J.pat.x, k = J.k;
   for (int i = threadIdx.x; i < 256; i += blockDim.x) s_lut[i] = (uint8_t)base_code((uint8_t)i);
@@ -53,19 +60,47 @@ __global__ void __launch_bounds__(kSegThreads) sketch_seg_kernel(const __grid_co
     s_delta[i] = (uint32_t)(i + 1 < x ? J.pat.off[i + 1] - J.pat.off[i] : p + J.pat.off[0] - J.pat.off[i]);
   }
   __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint8_t* wcodes = s_codes[wid];
   KT* B = reinterpret_cast<KT*>(seg_smem) + threadIdx.x * ROW;
   KT* C = B + W;
   const uint64_t mask = (k >= 32) ? ~0ULL : ((1ULL << (2 * k)) - 1);
   const uint32_t rshift = 2 * k - 2;
   const uint32_t xinv = 0xFFFFFFFFu / (uint32_t)x;
   const KT PALIN = (KT)~(KT)0;
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < J.n_seg; g += stride) {
-    const SegDesc d = J.segs[g];
+  const uint64_t n_groups = (J.n_seg + 31) / 32;
+  const uint64_t warps = (uint64_t)gridDim.x * WARPS;
+  // a warp takes 32 consecutive segments, one per lane
+  for (uint64_t grp = blockIdx.x * (uint64_t)WARPS + wid; grp < n_groups; grp += warps) {
+    const uint64_t g = grp * 32 + lane;
+    SegDesc d{0, 0, 0, 0, 0};
+    if (g < J.n_seg) d = J.segs[g];
     const uint32_t m = d.m;
-    const uint8_t* src = J.bytes + d.byte_off + d.shift;
+    const uint64_t s0 = d.byte_off + d.shift;     // first byte the segment may read
+    // one past its last kept base: orig(m - 1) + 1
+    uint64_t s1 = s0;
+    if (m) {
+      uint32_t q, rr;
+      divmod_x(m - 1, (uint32_t)x, xinv, q, rr);
+      s1 = s0 + (uint64_t)p * q + s_off[rr] + 1;
+    }
+    // the warp's byte span; staged (coded) in shared memory when it fits
+    uint64_t lo = m ? s0 : ~0ull, hi = m ? s1 : 0;
+#pragma unroll
+    for (int dd = 16; dd >= 1; dd >>= 1) {
+      const uint64_t olo = __shfl_xor_sync(FULL, lo, dd), ohi = __shfl_xor_sync(FULL, hi, dd);
+      lo = olo < lo ? olo : lo;
+      hi = ohi > hi ? ohi : hi;
+    }
+    const bool staged = hi > lo && hi - lo <= (uint64_t)kWarpBytes;
+    if (staged) {
+      const uint32_t span = (uint32_t)(hi - lo);
+      for (uint32_t b = lane; b < span; b += 32) wcodes[b] = s_lut[__ldg(J.bytes + lo + b)];
+    }
+    __syncwarp();
+    const uint8_t* src = J.bytes + s0;
+    const uint8_t* csrc = wcodes + (staged && m ? (uint32_t)(s0 - lo) : 0u);
     const uint32_t nk = m >= (uint32_t)k ? m - k + 1 : 0;
-    MinRec* out = a.staging + J.seg_voff[g];
     uint32_t cnt = 0;
     uint64_t fwd = 0, rev = 0;
     uint32_t run = 0, nflag = 0;
@@ -73,7 +108,7 @@ __global__ void __launch_bounds__(kSegThreads) sketch_seg_kernel(const __grid_co
     // bases of the first k - 1 positions
     const uint32_t pre = min(m, (uint32_t)k - 1);
     for (uint32_t i = 0; i < pre; ++i) {
-      const uint32_t c = s_lut[__ldg(src + o)];
+      const uint32_t c = staged ? csrc[o] : s_lut[__ldg(src + o)];
       o += s_delta[r];
       r = r + 1 == (uint32_t)x ? 0 : r + 1;
       nflag |= c >> 2;
@@ -89,6 +124,7 @@ __global__ void __launch_bounds__(kSegThreads) sketch_seg_kernel(const __grid_co
     }
     KT pm = 0, px = 0;
     uint32_t zr = 0;                            // strand bits of the last 32 k-mers (bit 0 = newest)
+    MinRec* out = a.staging + (g < J.n_seg ? J.seg_voff[g] : 0);
     const uint32_t steps = nk ? nk + W - 1 : 0;
     for (uint32_t j0 = 0; j0 < steps; j0 += W) {
 #pragma unroll
@@ -97,7 +133,7 @@ __global__ void __launch_bounds__(kSegThreads) sketch_seg_kernel(const __grid_co
         KT key = 0;
         uint32_t z = 0;
         if (j < nk) {
-          const uint32_t c = s_lut[__ldg(src + o)];
+          const uint32_t c = staged ? csrc[o] : s_lut[__ldg(src + o)];
           o += s_delta[r];
           r = r + 1 == (uint32_t)x ? 0 : r + 1;
           nflag |= c >> 2;
@@ -143,9 +179,12 @@ __global__ void __launch_bounds__(kSegThreads) sketch_seg_kernel(const __grid_co
         D[t] = max(C[t], D[t + 1]);
       }
     }
-    a.sub_cnt[g] = cnt;
-    if (J.seg_cnt) J.seg_cnt[g] = cnt;
-    if (nflag && (d.flags & kSegCapped) && J.read_flag) J.read_flag[d.read] = 1u;
+    if (g < J.n_seg) {
+      a.sub_cnt[g] = cnt;
+      if (J.seg_cnt) J.seg_cnt[g] = cnt;
+      if (nflag && (d.flags & kSegCapped) && J.read_flag) J.read_flag[d.read] = 1u;
+    }
+    __syncwarp();   // the staged bytes are rewritten by the next group
   }
 }
 

@@ -1,8 +1,8 @@
 """Batched launch machinery: results do not depend on how the work is launched.
 
-* The autotuner (several CTA shapes and tile sizes timed on the batch itself)
-  changes only the launch shape: anchors equal the fixed default's and the
-  oracle's, and its choices are recorded.
+* The autotuner (several CTA shapes and tile sizes of the tile kernel timed on
+  the batch itself) changes only the launch shape: anchors equal the fixed
+  default's and the oracle's, and its choices are recorded.
 * The CUDA-graph path (the sketch pass captured per call and applied to a
   cached executable with cudaGraphExecUpdate) gives the same anchors as direct
   launches, across calls whose sizes change between replays.
@@ -49,8 +49,11 @@ def test_autotuned_launch_same_anchors(env):
     ka, _, _ = god.god_index_export(base)
     kb, _, _ = god.god_index_export(tuned)
     assert np.array_equal(ka, kb)
+    # the reference's pass runs the tile kernel with a tuned shape; the reads'
+    # short segments run the one-thread-per-segment kernel, which has no shape
+    # to choose
     table = god.god_autotune_report()
-    assert len(table) >= 2 and all(e["threads"] in (128, 256) and e["chunks"] in (1, 2) for e in table)
+    assert len(table) >= 1 and all(e["threads"] in (128, 256) and e["chunks"] in (1, 2) for e in table)
 
 
 def test_graph_replay_matches_direct(env):
