@@ -4,8 +4,8 @@
 // long reads).
 //
 // A warp takes 32 consecutive segments, one per lane. Their bytes (for short
-// reads one contiguous span) are loaded by the whole warp with coalesced
-// loads, coded in 2 bits on the way, into shared memory; a span past 4 KB is
+// reads one contiguous span) are loaded by the whole warp as aligned 16-byte
+// words, coded in 2 bits on the way, into shared memory; a span past 4 KB is
 // read in place instead. Then each thread walks its segment base by base:
 //  * the kept base of patterned index j (orig = s + p (j / x) + off[j mod x],
 //    stepped incrementally) is taken in its 2-bit code and rolled into
@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(kSegThreads) sketch_seg_kernel(const __grid_co
   const unsigned FULL = 0xffffffffu;
   __shared__ uint8_t s_lut[256];
   __shared__ uint32_t s_off[kMaxPattern], s_delta[kMaxPattern];
-  __shared__ uint8_t s_codes[WARPS][kWarpBytes];   // the warp's bytes, already 2-bit coded
+  __shared__ __align__(16) uint8_t s_codes[WARPS][kWarpBytes];   // the warp's bytes, already 2-bit coded
   const SketchJob& J = a.job;
   const int p = J.pat.p, x = J.pat.x, k = J.k;
   for (int i = threadIdx.x; i < 256; i += blockDim.x) s_lut[i] = (uint8_t)base_code((uint8_t)i);
@@ -92,14 +92,32 @@ __global__ void __launch_bounds__(kSegThreads) sketch_seg_kernel(const __grid_co
       lo = olo < lo ? olo : lo;
       hi = ohi > hi ? ohi : hi;
     }
-    const bool staged = hi > lo && hi - lo <= (uint64_t)kWarpBytes;
+    // the span widened to aligned 16-byte words (every such word holds one of
+    // the span's bytes, so it lies in a mapped page of the read buffer)
+    const uintptr_t a0 = reinterpret_cast<uintptr_t>(J.bytes + lo) & ~(uintptr_t)15;
+    const uintptr_t a1 = (reinterpret_cast<uintptr_t>(J.bytes + hi) + 15) & ~(uintptr_t)15;
+    const bool staged = hi > lo && a1 - a0 <= (uintptr_t)kWarpBytes;
     if (staged) {
-      const uint32_t span = (uint32_t)(hi - lo);
-      for (uint32_t b = lane; b < span; b += 32) wcodes[b] = s_lut[__ldg(J.bytes + lo + b)];
+      const uint32_t nw = (uint32_t)((a1 - a0) >> 4);
+      const uint4* wsrc = reinterpret_cast<const uint4*>(a0);
+      uint4* wdst = reinterpret_cast<uint4*>(wcodes);
+#pragma unroll 4
+      for (uint32_t c = lane; c < nw; c += 32) {
+        const uint4 v = __ldg(wsrc + c);
+        const uint32_t in[4] = {v.x, v.y, v.z, v.w};
+        uint32_t outw[4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+          outw[h] = (uint32_t)s_lut[in[h] & 0xFFu] | ((uint32_t)s_lut[(in[h] >> 8) & 0xFFu] << 8) |
+                    ((uint32_t)s_lut[(in[h] >> 16) & 0xFFu] << 16) | ((uint32_t)s_lut[in[h] >> 24] << 24);
+        }
+        wdst[c] = make_uint4(outw[0], outw[1], outw[2], outw[3]);
+      }
     }
     __syncwarp();
     const uint8_t* src = J.bytes + s0;
-    const uint8_t* csrc = wcodes + (staged && m ? (uint32_t)(s0 - lo) : 0u);
+    const uint8_t* csrc =
+        wcodes + (staged && m ? (uint32_t)(reinterpret_cast<uintptr_t>(J.bytes + s0) - a0) : 0u);
     const uint32_t nk = m >= (uint32_t)k ? m - k + 1 : 0;
     uint32_t cnt = 0;
     uint64_t fwd = 0, rev = 0;

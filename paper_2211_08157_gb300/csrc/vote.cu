@@ -15,8 +15,9 @@
 //     vote beyond; closed groups with at least V votes enter a top list kept
 //     one entry per lane (votes descending, discovery order on ties, cut at
 //     max_out), and the group with the most votes is kept as the rescue.
-// Lists of up to 32 votes are sorted in registers by a warp (bitonic network
-// over shuffles); longer ones by a CTA in shared memory (bitonic network up to
+// Lists of up to 16 votes are sorted in one thread's registers and walked by
+// that thread (when at most 8 winners are kept); up to 32 by a warp (bitonic
+// network over shuffles, then the warp's walk); longer ones by a CTA in shared memory (bitonic network up to
 // 4096 keys), and lists past 4096 in sorted chunks merged by merge-path
 // passes in a global buffer. CTAs take long reads from a shared counter,
 // chunked ones first.
@@ -28,6 +29,8 @@ namespace god {
 namespace {
 
 constexpr int kVT = 256;                 // threads of the CTA path
+constexpr uint32_t kVoteThreadCap = 16;  // votes sorted in one thread's registers
+constexpr uint32_t kThreadTop = 8;       // winners a thread keeps (max_out <= 8 for the thread path)
 constexpr uint32_t kVoteWarpCap = 32;    // votes sorted in registers by one warp
 constexpr uint32_t kVoteCap = 4096;      // votes sorted in shared memory at once
 constexpr int kIdxBits = 28;             // anchor index field of the sort key
@@ -74,15 +77,17 @@ __device__ __forceinline__ void warp_push(bool f, uint32_t v, uint32_t* list, un
 }
 
 // counts[r] = 0 for reads without anchors; lists of reads by vote count.
-// ctl: [0] warp list, [1] long list, [2] chunked list, [3] queue, [4] error.
+// ctl: [0] warp list, [1] long list, [2] chunked list, [3] queue, [4] error,
+// [5] thread list (when max_out allows it).
 __global__ void vote_classify(uint32_t n, const uint64_t* __restrict__ read_off, uint32_t* __restrict__ counts,
                               uint32_t* __restrict__ lw, uint32_t* __restrict__ ll, uint32_t* __restrict__ lh,
-                              unsigned int* ctl) {
+                              uint32_t* __restrict__ lt, uint32_t thread_cap, unsigned int* ctl) {
   for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < n; r += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t c = read_off[r + 1] - read_off[r];
     if (c == 0) counts[r] = 0;
     if (c > kIdxMask) atomicExch(reinterpret_cast<int*>(ctl + 4), 2);
-    warp_push(c > 0 && c <= kVoteWarpCap, (uint32_t)r, lw, ctl + 0);
+    warp_push(c > 0 && c <= thread_cap, (uint32_t)r, lt, ctl + 5);
+    warp_push(c > thread_cap && c <= kVoteWarpCap, (uint32_t)r, lw, ctl + 0);
     warp_push(c > kVoteWarpCap && c <= kVoteCap, (uint32_t)r, ll, ctl + 1);
     warp_push(c > kVoteCap && c <= kIdxMask, (uint32_t)r, lh, ctl + 2);
   }
@@ -187,6 +192,112 @@ __device__ void vote_walk(uint32_t r, uint32_t n, const VoteCfg& cfg, Get get, g
     out[(uint64_t)r * cfg.max_out + lane] = rec;
   }
   if (lane == 0) counts[r] = total;
+}
+
+__device__ __forceinline__ void cswap64(uint64_t& x, uint64_t& y, bool up) {
+  const uint64_t lo = x < y ? x : y, hi = x < y ? y : x;
+  x = up ? lo : hi;
+  y = up ? hi : lo;
+}
+
+// Reads with at most 16 votes (and max_out <= 8): a thread per read. The keys
+// are sorted by a 16-wide bitonic network in registers, the groups walked in
+// order, and the winners kept in a register top list (insertion at the
+// number of kept winners with at least as many votes: equal votes keep their
+// (strand, v0) order).
+constexpr int kVTT = 128;   // threads per block of the thread path (many registers per thread)
+
+__global__ void __launch_bounds__(kVTT) vote_thread(const god_anchor* __restrict__ a,
+                                                   const uint64_t* __restrict__ read_off,
+                                                   const uint64_t* __restrict__ offs, const uint32_t* __restrict__ list,
+                                                   const unsigned int* __restrict__ ctl, VoteCfg cfg,
+                                                   god_vote_rec* __restrict__ out, uint32_t* __restrict__ counts) {
+  const uint32_t nl = ctl[5];
+  for (uint64_t li = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; li < nl; li += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t r = list[li];
+    const uint64_t lo = read_off[r];
+    const uint32_t n = (uint32_t)(read_off[r + 1] - lo);
+    const uint64_t len = offs[r + 1] - offs[r];
+    uint64_t kk[kVoteThreadCap];
+#pragma unroll
+    for (int q = 0; q < (int)kVoteThreadCap; ++q) kk[q] = (uint32_t)q < n ? vote_key(a[lo + q], len, q) : ~0ull;
+#pragma unroll
+    for (int s2 = 2; s2 <= (int)kVoteThreadCap; s2 <<= 1) {
+#pragma unroll
+      for (int j = s2 >> 1; j > 0; j >>= 1) {
+#pragma unroll
+        for (int q = 0; q < (int)kVoteThreadCap; ++q) {
+          const int q2 = q ^ j;
+          if (q2 > q) cswap64(kk[q], kk[q2], (q & s2) == 0);
+        }
+      }
+    }
+    Group e[kThreadTop];
+    uint32_t cnt = 0;
+    Group best{0, 0, 0, 0, 0, 0, 0};
+    Group g{0, 0, 0, 0, 0, 0, 0};
+    auto close = [&](const Group& c) {
+      if (c.votes >= cfg.V) {
+        uint32_t pos = 0;
+#pragma unroll
+        for (int q = 0; q < (int)kThreadTop; ++q) pos += ((uint32_t)q < cnt && e[q].votes >= c.votes) ? 1u : 0u;
+        if (pos < cfg.max_out) {
+#pragma unroll
+          for (int q = (int)kThreadTop - 1; q > 0; --q)
+            if ((uint32_t)q > pos) e[q] = e[q - 1];
+#pragma unroll
+          for (int q = 0; q < (int)kThreadTop; ++q)
+            if ((uint32_t)q == pos) e[q] = c;
+          cnt = min(cnt + 1, cfg.max_out);
+        }
+      }
+      if (c.votes > best.votes) best = c;   // groups have >= 1 vote: the first one always enters
+    };
+#pragma unroll
+    for (int q = 0; q < (int)kVoteThreadCap; ++q) {
+      if ((uint32_t)q < n) {
+        const uint64_t key = kk[q];
+        const god_anchor an = a[lo + (key & kIdxMask)];
+        const uint32_t st = key_strand(key);
+        const int64_t v = key_v(key);
+        if (q > 0 && (st != g.strand || v - g.v0 > (int64_t)cfg.D)) close(g);
+        if (q == 0 || st != g.strand || v - g.v0 > (int64_t)cfg.D) {
+          g.strand = st;
+          g.v0 = v;
+          g.votes = 0;
+          g.ref_lo = g.read_lo = 0xffffffffu;
+          g.ref_hi = g.read_hi = 0;
+        }
+        g.votes++;
+        g.ref_lo = min(g.ref_lo, an.ref_pos);
+        g.ref_hi = max(g.ref_hi, an.ref_pos);
+        g.read_lo = min(g.read_lo, an.read_pos);
+        g.read_hi = max(g.read_hi, an.read_pos);
+      }
+    }
+    close(g);
+    const bool rescue = cnt == 0;
+    const uint32_t total = rescue ? 1u : cnt;
+    god_vote_rec* o = out + (uint64_t)r * cfg.max_out;
+#pragma unroll
+    for (int q = 0; q < (int)kThreadTop; ++q) {
+      if ((uint32_t)q < total) {
+        const Group& s = rescue ? best : e[q];
+        god_vote_rec rec;
+        rec.read_id = r;
+        rec.votes = s.votes;
+        rec.strand = s.strand;
+        rec.rescue = rescue ? 1u : 0u;
+        rec.loc = s.v0;
+        rec.ref_lo = s.ref_lo;
+        rec.ref_hi = s.ref_hi;
+        rec.read_lo = s.read_lo;
+        rec.read_hi = s.read_hi;
+        o[q] = rec;
+      }
+    }
+    counts[r] = total;
+  }
 }
 
 // Reads with at most 32 votes: a warp per read, keys sorted in registers.
@@ -373,7 +484,7 @@ int vote_device(const god_anchor* d_a, uint64_t m, const uint64_t* d_offs, uint3
   DBuf<uint32_t> lists;
   DBuf<unsigned int> ctl;
   GOD_TRY(read_off.alloc((uint64_t)n + 1, st));
-  GOD_TRY(lists.alloc(3 * (uint64_t)n, st));
+  GOD_TRY(lists.alloc(4 * (uint64_t)n, st));
   GOD_TRY(ctl.alloc(8, st));
   GOD_CK(cudaMemsetAsync(ctl.p, 0, 8 * sizeof(unsigned int), st));
   int* err = reinterpret_cast<int*>(ctl.p + 4);
@@ -381,7 +492,10 @@ int vote_device(const god_anchor* d_a, uint64_t m, const uint64_t* d_offs, uint3
   uint32_t* lw = lists.p;
   uint32_t* ll = lists.p + n;
   uint32_t* lh = lists.p + 2 * (uint64_t)n;
-  GOD_LAUNCH(vote_classify, grid_for(n, kVT, 32), kVT, 0, st, n, read_off.p, d_counts, lw, ll, lh, ctl.p);
+  uint32_t* lt = lists.p + 3 * (uint64_t)n;
+  const uint32_t thread_cap = p.max_out <= kThreadTop ? kVoteThreadCap : 0;
+  GOD_LAUNCH(vote_classify, grid_for(n, kVT, 32), kVT, 0, st, n, read_off.p, d_counts, lw, ll, lh, lt, thread_cap,
+             ctl.p);
   unsigned int h[8];
   GOD_CK(cudaMemcpyAsync(h, ctl.p, sizeof h, cudaMemcpyDeviceToHost, st));
   GOD_CK(cudaStreamSynchronize(st));
@@ -393,6 +507,9 @@ int vote_device(const god_anchor* d_a, uint64_t m, const uint64_t* d_offs, uint3
     set_error("vote: a read has 2^28 anchors or more");
     return GOD_EINVAL;
   }
+  if (h[5])
+    GOD_LAUNCH(vote_thread, grid_for(h[5], kVTT, 24), kVTT, 0, st, d_a, read_off.p, d_offs, lt, ctl.p, cfg, d_out,
+               d_counts);
   if (h[0])
     GOD_LAUNCH(vote_warp, grid_for((uint64_t)h[0] * 32, kVT, 16), kVT, 0, st, d_a, read_off.p, d_offs, lw, ctl.p, cfg,
                d_out, d_counts);
@@ -404,7 +521,7 @@ int vote_device(const god_anchor* d_a, uint64_t m, const uint64_t* d_offs, uint3
   }
   // algorithmic bytes: one 16-byte anchor read per vote, the read ranges, one
   // record written per reported group
-  prof_add_work("vote_warp", 16.0 * (double)m, (double)m);
+  prof_add_work(h[5] ? "vote_thread" : "vote_warp", 16.0 * (double)m, (double)m);
   return GOD_OK;
 }
 
