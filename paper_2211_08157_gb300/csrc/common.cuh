@@ -161,6 +161,8 @@ struct SketchJob {
   int tune;                   // 1: pick the launch shape with the autotuner (cached per shape class)
   uint32_t max_m;             // longest segment's m when known (0 = unknown); batches of short
                               // segments then run the one-thread-per-segment kernel
+  int bytes_on_host;          // 1: `bytes` is page-locked host memory read over the host link
+                              // (the per-segment kernel then stages each warp's span with wide loads)
 };
 
 // Runs the fused sparsify + 2-bit code + hash + window-minimum kernel over the

@@ -830,6 +830,7 @@ int sketch_and_lookup(const god_index* idx, const uint8_t* d_reads, SetBufs& B, 
   job.read_flag = read_flag;
   job.tune = idx->params.tune;
   job.max_m = max_m;
+  job.bytes_on_host = is_device_ptr(d_reads) ? 0 : 1;
   StagedSketch SS;
   GOD_TRY(run_sketch_staged(job, st, SS, nullptr));
   B.n_rec = SS.total;
