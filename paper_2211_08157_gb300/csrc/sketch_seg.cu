@@ -45,15 +45,14 @@ struct SegArgs {
   uint32_t* sub_cnt;
 };
 
-template <typename KT, int HM, int W>
-__global__ void __launch_bounds__(kSegThreads) sketch_seg_kernel(const __grid_constant__ SegArgs a) {
+template <typename KT, int HM, int W, bool STAGE>
+__global__ void __launch_bounds__(kSegThreads, (W <= 11 ? 6 : 3)) sketch_seg_kernel(const __grid_constant__ SegArgs a) {
   extern __shared__ __align__(16) unsigned char seg_smem[];
   constexpr int ROW = 2 * W + 1;              // keys B[W], minima C[W]; odd stride: no bank conflicts
   constexpr int WARPS = kSegThreads / 32;
   const unsigned FULL = 0xffffffffu;
   __shared__ uint8_t s_lut[256];
   __shared__ uint32_t s_off[kMaxPattern], s_delta[kMaxPattern];
-  __shared__ __align__(16) uint8_t s_codes[WARPS][kWarpBytes];   // the warp's bytes, already 2-bit coded
   const SketchJob& J = a.job;
   const int p = J.pat.p, x = J.pat.x, k = J.k;
   for (int i = threadIdx.x; i < 256; i += blockDim.x) s_lut[i] = (uint8_t)base_code((uint8_t)i);
@@ -63,8 +62,9 @@ __global__ void __launch_bounds__(kSegThreads) sketch_seg_kernel(const __grid_co
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  uint8_t* wcodes = s_codes[wid];
   KT* B = reinterpret_cast<KT*>(seg_smem) + threadIdx.x * ROW;
+  // the warp's staged bytes, already 2-bit coded (present when staging)
+  uint8_t* wcodes = seg_smem + (size_t)kSegThreads * ROW * sizeof(KT) + (size_t)wid * kWarpBytes;
   KT* C = B + W;
   const uint64_t mask = (k >= 32) ? ~0ULL : ((1ULL << (2 * k)) - 1);
   const uint32_t rshift = 2 * k - 2;
@@ -88,18 +88,20 @@ __global__ void __launch_bounds__(kSegThreads) sketch_seg_kernel(const __grid_co
     }
     // the warp's byte span; staged (coded) in shared memory when it fits
     uint64_t lo = m ? s0 : ~0ull, hi = m ? s1 : 0;
+    if (STAGE) {
 #pragma unroll
-    for (int dd = 16; dd >= 1; dd >>= 1) {
-      const uint64_t olo = __shfl_xor_sync(FULL, lo, dd), ohi = __shfl_xor_sync(FULL, hi, dd);
-      lo = olo < lo ? olo : lo;
-      hi = ohi > hi ? ohi : hi;
+      for (int dd = 16; dd >= 1; dd >>= 1) {
+        const uint64_t olo = __shfl_xor_sync(FULL, lo, dd), ohi = __shfl_xor_sync(FULL, hi, dd);
+        lo = olo < lo ? olo : lo;
+        hi = ohi > hi ? ohi : hi;
+      }
     }
     // the span widened to aligned 16-byte words (every such word holds one of
     // the span's bytes, so it lies in a mapped page of the read buffer)
     const uintptr_t a0 = reinterpret_cast<uintptr_t>(J.bytes + lo) & ~(uintptr_t)15;
     const uintptr_t a1 = (reinterpret_cast<uintptr_t>(J.bytes + hi) + 15) & ~(uintptr_t)15;
-    const bool staged = J.bytes_on_host && hi > lo && a1 - a0 <= (uintptr_t)kWarpBytes;
-    if (staged) {
+    const bool staged = STAGE && hi > lo && a1 - a0 <= (uintptr_t)kWarpBytes;
+    if (STAGE && staged) {
       const uint32_t nw = (uint32_t)((a1 - a0) >> 4);
       const uint4* wsrc = reinterpret_cast<const uint4*>(a0);
       uint4* wdst = reinterpret_cast<uint4*>(wcodes);
@@ -128,7 +130,7 @@ __global__ void __launch_bounds__(kSegThreads) sketch_seg_kernel(const __grid_co
     // bases of the first k - 1 positions
     const uint32_t pre = min(m, (uint32_t)k - 1);
     for (uint32_t i = 0; i < pre; ++i) {
-      const uint32_t c = staged ? csrc[o] : s_lut[__ldg(src + o)];
+      const uint32_t c = (STAGE && staged) ? csrc[o] : s_lut[__ldg(src + o)];
       o += s_delta[r];
       r = r + 1 == (uint32_t)x ? 0 : r + 1;
       nflag |= c >> 2;
@@ -153,7 +155,7 @@ __global__ void __launch_bounds__(kSegThreads) sketch_seg_kernel(const __grid_co
         KT key = 0;
         uint32_t z = 0;
         if (j < nk) {
-          const uint32_t c = staged ? csrc[o] : s_lut[__ldg(src + o)];
+          const uint32_t c = (STAGE && staged) ? csrc[o] : s_lut[__ldg(src + o)];
           o += s_delta[r];
           r = r + 1 == (uint32_t)x ? 0 : r + 1;
           nflag |= c >> 2;
@@ -210,8 +212,9 @@ __global__ void __launch_bounds__(kSegThreads) sketch_seg_kernel(const __grid_co
 
 template <typename KT, int HM, int W>
 int launch_seg(const SegArgs& a, cudaStream_t st) {
-  auto sketch_seg = sketch_seg_kernel<KT, HM, W>;
-  const size_t smem = (size_t)kSegThreads * (2 * W + 1) * sizeof(KT);
+  auto sketch_seg = a.job.bytes_on_host ? sketch_seg_kernel<KT, HM, W, true> : sketch_seg_kernel<KT, HM, W, false>;
+  const size_t rows = ((size_t)kSegThreads * (2 * W + 1) * sizeof(KT) + 15) & ~(size_t)15;
+  const size_t smem = rows + (a.job.bytes_on_host ? (size_t)(kSegThreads / 32) * kWarpBytes : 0);
   GOD_CK(cudaFuncSetAttribute(sketch_seg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   GOD_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sketch_seg, kSegThreads, smem));
