@@ -633,8 +633,11 @@ def main():
     seed_only = {}
     index_build = {}
     if not args.no_compare:
-        for nm, kd in (("hash", god.GOD_INDEX_HASH), ("learned", god.GOD_INDEX_LEARNED)):
+        for nm, kd in (("hash", god.GOD_INDEX_HASH), ("learned", god.GOD_INDEX_LEARNED),
+                       ("learned_readout_only", god.GOD_INDEX_LEARNED)):
             prm = god.god_params_init(index_kind=kd, pa_t=wl.t)
+            if nm == "learned_readout_only":
+                prm.rmi_train_steps = 0          # the least-squares output layer without the Adam steps
             bt = []
             idx = None
             for _ in range(3):
@@ -671,9 +674,10 @@ def main():
             if nm == "hash":
                 seed_only["vote"] = vote_line(god, torch, dev, stream, flush, idx, d_reads, d_offs, bases,
                                               long_reads=False)
-            if nm == "learned":
+            if nm.startswith("learned"):
                 seed_only[nm].update(rmi_mean_eps=info["rmi_mean_eps"], rmi_leaves=info["rmi_leaves"],
-                                     rmi_fallback_key_frac=info["rmi_fallback_key_frac"])
+                                     rmi_fallback_key_frac=info["rmi_fallback_key_frac"],
+                                     rmi_final_loss=info["rmi_final_loss"])
             idx.close()
 
     # ---- end to end through the C ABI with pinned host buffers

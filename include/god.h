@@ -401,10 +401,12 @@ int god_server_create(const god_index *idx, const god_server_config *cfg, god_se
 int god_server_submit(god_server *s, const uint8_t *reads, const uint64_t *offsets, uint32_t n,
                       uint64_t *request_id);
 /* Waits up to timeout_ms (negative = forever) for a request. On GOD_OK the
- * anchors (read_id local to the request) are returned as a malloc'ed host
- * array (release with god_free) and, if latency_s is not NULL, the time from
- * submit to completion; GOD_EBUSY if it is not done in time. A request that
- * alone exceeds the memory budget completes with GOD_ENOMEM. */
+ * anchors (read_id local to the request) are returned as a host array
+ * (release with god_free: a slice of the page-locked buffer that received its
+ * batch's anchors, which returns to the server's pool once every slice of it
+ * is freed, also after god_server_destroy) and, if latency_s is not NULL, the
+ * time from submit to completion; GOD_EBUSY if it is not done in time. A
+ * request that alone exceeds the memory budget completes with GOD_ENOMEM. */
 int god_server_wait(god_server *s, uint64_t request_id, int timeout_ms, god_anchor **anchors,
                     uint64_t *n_anchors, double *latency_s);
 

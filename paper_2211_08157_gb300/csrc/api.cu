@@ -225,11 +225,13 @@ int parse_pattern(const char* s, PatternInfo* out) {
 }
 
 // ---- ownership registry for god_free
-enum class Kind { Index, HostArray, DeviceArray };
+enum class Kind { Index, HostArray, DeviceArray, Slice };
 struct Owned {
   Kind kind;
   cudaStream_t stream;
   int device;
+  void (*release)(void*);   // Slice: called with ctx when the slice is freed
+  void* ctx;
 };
 static std::mutex g_reg_mu;
 static std::unordered_map<void*, Owned> g_reg;
@@ -238,11 +240,17 @@ static void reg_add(void* p, Kind k, cudaStream_t st) {
   int dev = 0;
   cudaGetDevice(&dev);
   std::lock_guard<std::mutex> lk(g_reg_mu);
-  g_reg[p] = Owned{k, st, dev};
+  g_reg[p] = Owned{k, st, dev, nullptr, nullptr};
 }
 
 void register_host_array(void* p) {
   if (p) reg_add(p, Kind::HostArray, 0);
+}
+
+void register_slice(void* p, void (*release)(void*), void* ctx) {
+  if (!p) return;
+  std::lock_guard<std::mutex> lk(g_reg_mu);
+  g_reg[p] = Owned{Kind::Slice, 0, 0, release, ctx};
 }
 
 // Device address of page-locked host memory (readable and writable by kernels
@@ -863,6 +871,7 @@ void god_free(void* p) {
   switch (o.kind) {
     case Kind::Index: free_index(static_cast<god_index*>(p)); break;
     case Kind::HostArray: free(p); break;
+    case Kind::Slice: o.release(o.ctx); break;
     case Kind::DeviceArray: {
       int prev = 0;
       cudaGetDevice(&prev);

@@ -102,6 +102,8 @@ struct DBuf {
 bool is_device_ptr(const void* p);
 // Hands a malloc'ed host array to god_free's ownership registry.
 void register_host_array(void* p);
+// Hands a pointer into a shared buffer to god_free: freeing it calls release(ctx).
+void register_slice(void* p, void (*release)(void*), void* ctx);
 
 // ------------------------------------------------------------------ pattern
 constexpr int kMaxPattern = 64;

@@ -7,7 +7,9 @@
 // the budget has left. The merged batch runs through the same batched seeding
 // pass as god_seed (one sketch launch over all of its reads), then the sorted
 // anchor list is cut back into per-request arrays by read range (anchors are
-// sorted by read, so each request owns one contiguous run). Slots run
+// sorted by read, so each request owns one contiguous run) without a copy: the
+// batch's anchors land in one page-locked buffer whose slices are the
+// requests' results. Slots run
 // concurrently, so requests that arrive while others are on the GPU overlap
 // with them. Integer results do not depend on how requests were merged.
 #include <algorithm>
@@ -26,6 +28,8 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
+struct Arena;
+
 struct Request {
   uint64_t id;
   const uint8_t* reads = nullptr;   // the caller's bytes (valid until its wait returns)
@@ -36,9 +40,94 @@ struct Request {
   bool done = false;
   bool merged = false;
   int rc = GOD_OK;
-  god_anchor* result = nullptr;
+  god_anchor* result = nullptr;   // a slice of `arena`, or malloc'ed when empty
+  Arena* arena = nullptr;
   uint64_t n_result = 0;
 };
+
+// Page-locked buffer holding one batch's anchors; every request of the batch
+// gets its result as a slice of it (no per-request copy), and the buffer goes
+// back to the server's pool when the last slice has been freed (god_free).
+struct ResultPool;
+struct Arena {
+  god_anchor* p = nullptr;
+  uint64_t cap = 0;
+  int refs = 0;                 // live slices, guarded by pool->mu
+  ResultPool* pool = nullptr;   // null once the server is gone
+};
+struct ResultPool {
+  std::mutex mu;
+  std::vector<Arena*> free_list;
+  std::vector<Arena*> all;
+};
+
+void arena_release(void* ctx) {
+  Arena* a = static_cast<Arena*>(ctx);
+  ResultPool* pool = a->pool;
+  if (!pool) {   // the server is gone: the last slice frees the buffer
+    if (--a->refs == 0) {
+      cudaFreeHost(a->p);
+      delete a;
+    }
+    return;
+  }
+  std::lock_guard<std::mutex> lk(pool->mu);
+  if (--a->refs == 0) pool->free_list.push_back(a);
+}
+
+// A free arena of at least `need` anchors (the smallest that fits), or a new one.
+Arena* arena_take(ResultPool* pool, uint64_t need) {
+  {
+    std::lock_guard<std::mutex> lk(pool->mu);
+    size_t best = pool->free_list.size();
+    for (size_t i = 0; i < pool->free_list.size(); ++i)
+      if (pool->free_list[i]->cap >= need && (best == pool->free_list.size() ||
+                                                pool->free_list[i]->cap < pool->free_list[best]->cap))
+        best = i;
+    if (best < pool->free_list.size()) {
+      Arena* a = pool->free_list[best];
+      pool->free_list.erase(pool->free_list.begin() + best);
+      return a;
+    }
+  }
+  Arena* a = new Arena();
+  a->cap = std::max<uint64_t>(need, 1ull << 20);
+  if (cudaMallocHost(&a->p, a->cap * sizeof(god_anchor)) != cudaSuccess) {
+    cudaGetLastError();
+    delete a;
+    return nullptr;
+  }
+  a->pool = pool;
+  std::lock_guard<std::mutex> lk(pool->mu);
+  pool->all.push_back(a);
+  return a;
+}
+
+// memcpy of a batch's request bytes into the pinned staging buffer, split over
+// a few threads when it is large (one thread copies well below the memory
+// bandwidth of the host).
+void gather_bytes(const std::vector<std::pair<const uint8_t*, uint64_t>>& parts, uint8_t* dst) {
+  uint64_t total = 0;
+  for (auto& pr : parts) total += pr.second;
+  const int nt = total >= (16ull << 20) ? 4 : 1;
+  auto copy_range = [&](uint64_t lo, uint64_t hi) {   // byte range [lo, hi) of the concatenation
+    uint64_t at = 0;
+    for (auto& pr : parts) {
+      const uint64_t a = std::max(lo, at), b = std::min(hi, at + pr.second);
+      if (a < b) memcpy(dst + a, pr.first + (a - at), b - a);
+      at += pr.second;
+      if (at >= hi) break;
+    }
+  };
+  if (nt == 1) {
+    copy_range(0, total);
+    return;
+  }
+  std::vector<std::thread> th;
+  for (int i = 1; i < nt; ++i) th.emplace_back(copy_range, total * i / nt, total * (i + 1) / nt);
+  copy_range(0, total / nt);
+  for (auto& t : th) t.join();
+}
 
 // Device bytes a batch may hold at its peak: input, segment tables, minimizer
 // records, lookups and the anchor output (estimated at 2 anchors per kept
@@ -106,6 +195,7 @@ struct god_server {
   uint64_t inflight = 0;
   bool stop = false;
   god_server_stats st{};
+  ResultPool pool;
 };
 
 namespace {
@@ -116,8 +206,7 @@ void worker_main(god_server* S, int slot) {
   cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking);
   uint8_t* h_reads = nullptr;
   uint64_t* h_offs = nullptr;
-  god_anchor* h_out = nullptr;
-  size_t cap_reads = 0, cap_offs = 0, cap_out = 0;
+  size_t cap_reads = 0, cap_offs = 0;
   (void)slot;
   while (true) {
     std::vector<Request*> batch;
@@ -191,14 +280,16 @@ void worker_main(god_server* S, int slot) {
     std::vector<uint64_t> first_read;
     if (rc == GOD_OK) {
       uint64_t bo = 0, ro = 0;
+      std::vector<std::pair<const uint8_t*, uint64_t>> parts;
       for (Request* r : batch) {
-        memcpy(h_reads + bo, r->reads, r->bases);
+        parts.emplace_back(r->reads, r->bases);
         for (uint32_t i = 0; i < r->n; ++i) h_offs[ro + i] = bo + r->offs[i];
         first_read.push_back(ro);
         bo += r->bases;
         ro += r->n;
       }
       h_offs[ro] = bo;
+      gather_bytes(parts, h_reads);
     }
     // ---- device pass
     god::DBuf<uint8_t> d_reads;
@@ -216,10 +307,10 @@ void worker_main(god_server* S, int slot) {
       rc = god::seed_device(S->idx, d_reads.p, d_offs.p, (uint32_t)n, bases, o, stream, &d_out, &total, nullptr, 0,
                             true);
     }
-    if (rc == GOD_OK && total > cap_out) {
-      if (h_out) cudaFreeHost(h_out);
-      cap_out = std::max<uint64_t>(total, 1 << 16);
-      if (cudaMallocHost(&h_out, cap_out * sizeof(god_anchor)) != cudaSuccess) { h_out = nullptr; cap_out = 0; rc = GOD_ENOMEM; }
+    Arena* arena = nullptr;
+    if (rc == GOD_OK && total) {
+      arena = arena_take(&S->pool, total);
+      if (!arena) rc = GOD_ENOMEM;
     }
     // request boundaries and per-request read ids on the device, so the
     // split below is one copy per request
@@ -236,24 +327,37 @@ void worker_main(god_server* S, int slot) {
     if (rc == GOD_OK)
       rc = cudaMemcpyAsync(bounds.data(), d_bounds.p, (m + 1) * 8, cudaMemcpyDeviceToHost, stream) ? GOD_ECUDA : GOD_OK;
     if (rc == GOD_OK && total)
-      rc = cudaMemcpyAsync(h_out, d_out, total * sizeof(god_anchor), cudaMemcpyDeviceToHost, stream) ? GOD_ECUDA : GOD_OK;
+      rc = cudaMemcpyAsync(arena->p, d_out, total * sizeof(god_anchor), cudaMemcpyDeviceToHost, stream) ? GOD_ECUDA
+                                                                                                     : GOD_OK;
     if (d_out) god::dfree(d_out, stream);
     d_first.release();
     d_bounds.release();
     d_reads.release();
     d_offs.release();
     if (cudaStreamSynchronize(stream) != cudaSuccess && rc == GOD_OK) rc = GOD_ECUDA;
-    // ---- split per request
+    // ---- split per request: slices of the arena (an empty result gets a
+    // small host array of its own, so that every result pointer is distinct)
+    int slices = 0;
     for (size_t bi = 0; bi < batch.size(); ++bi) {
       Request* r = batch[bi];
       r->rc = rc;
       if (rc == GOD_OK) {
         r->n_result = bounds[bi + 1] - bounds[bi];
-        r->result = (god_anchor*)malloc(std::max<uint64_t>(r->n_result, 1) * sizeof(god_anchor));
-        if (!r->result) r->rc = GOD_ENOMEM;
-        else if (r->n_result) memcpy(r->result, h_out + bounds[bi], r->n_result * sizeof(god_anchor));
+        if (r->n_result) {
+          r->result = arena->p + bounds[bi];
+          r->arena = arena;
+          ++slices;
+        } else {
+          r->result = (god_anchor*)malloc(sizeof(god_anchor));
+          if (!r->result) r->rc = GOD_ENOMEM;
+        }
       }
       r->merged = batch.size() > 1;
+    }
+    if (arena) {
+      std::lock_guard<std::mutex> lk(S->pool.mu);
+      arena->refs += slices;
+      if (arena->refs == 0) S->pool.free_list.push_back(arena);
     }
     {
       std::lock_guard<std::mutex> lk(S->mu);
@@ -271,7 +375,6 @@ void worker_main(god_server* S, int slot) {
   }
   if (h_reads) cudaFreeHost(h_reads);
   if (h_offs) cudaFreeHost(h_offs);
-  if (h_out) cudaFreeHost(h_out);
   cudaStreamDestroy(stream);
 }
 
@@ -356,7 +459,10 @@ int god_server_wait(god_server* S, uint64_t id, int timeout_ms, god_anchor** anc
   if (rc == GOD_OK) {
     *anchors = r->result;
     *n_anchors = r->n_result;
-    god::register_host_array(r->result);
+    if (r->arena) god::register_slice(r->result, arena_release, r->arena);
+    else god::register_host_array(r->result);
+  } else if (r->arena) {
+    arena_release(r->arena);
   } else if (r->result) {
     free(r->result);
   }
@@ -380,8 +486,21 @@ int god_server_destroy(god_server* S) {
   S->cv_work.notify_all();
   for (auto& t : S->workers) t.join();
   for (auto& kv : S->reqs) {
-    if (kv.second->result) free(kv.second->result);
+    if (kv.second->arena) arena_release(kv.second->arena);
+    else if (kv.second->result) free(kv.second->result);
     delete kv.second;
+  }
+  {
+    // arenas with live slices outlive the server; the last slice frees them
+    std::lock_guard<std::mutex> lk(S->pool.mu);
+    for (Arena* a : S->pool.all) {
+      if (a->refs == 0) {
+        cudaFreeHost(a->p);
+        delete a;
+      } else {
+        a->pool = nullptr;
+      }
+    }
   }
   delete S;
   return GOD_OK;

@@ -87,13 +87,15 @@ def test_learned_seed_equals_hash_and_oracle(god):
 
 
 def test_trained_root_ablation(god, capsys):
-    """What the trained network gains: vs the same network untrained, and vs
-    no network at all (linear root)."""
+    """What the trained network gains: vs the same network untrained, vs its
+    least-squares output layer alone (no Adam steps), and vs no network at
+    all (linear root)."""
     ref = _ref(8_000_000, 33)
     res = {}
-    for name, kind in [("trained", god.GOD_ROOT_MLP), ("untrained", god.GOD_ROOT_UNTRAINED),
-                       ("linear", god.GOD_ROOT_LINEAR)]:
-        params = god.god_params_init(index_kind=god.GOD_INDEX_LEARNED, rmi_root=kind, rmi_leaf_bits=16)
+    for name, kind, steps in [("trained", god.GOD_ROOT_MLP, 64), ("readout", god.GOD_ROOT_MLP, 0),
+                              ("untrained", god.GOD_ROOT_UNTRAINED, 64), ("linear", god.GOD_ROOT_LINEAR, 64)]:
+        params = god.god_params_init(index_kind=god.GOD_INDEX_LEARNED, rmi_root=kind, rmi_leaf_bits=16,
+                                     rmi_train_steps=steps)
         idx = god.god_build_index(ref, "10", 21, 11, 500, params=params)
         info = idx.info
         res[name] = info
@@ -106,7 +108,8 @@ def test_trained_root_ablation(god, capsys):
         for k, v in res.items():
             print(f"\n[ablation] {k:9s} loss={v['rmi_final_loss']:.3g} mean_eps={v['rmi_mean_eps']:.2f} "
                   f"max_eps={v['rmi_max_eps']} fallback_keys={v['rmi_fallback_key_frac']:.4f}")
-    t, u, l = res["trained"], res["untrained"], res["linear"]
+    t, r, u, l = res["trained"], res["readout"], res["untrained"], res["linear"]
+    assert t["rmi_final_loss"] <= r["rmi_final_loss"]      # Adam keeps the better of the two
     assert t["rmi_mean_eps"] < 0.25 * u["rmi_mean_eps"]
     assert t["rmi_fallback_key_frac"] <= u["rmi_fallback_key_frac"]
     assert t["rmi_fallback_key_frac"] < 0.01
