@@ -79,7 +79,8 @@ typedef struct {
   int rmi_leaf_bits;       /* learned index: 2^bits leaves, 16..20; 0 = chosen from the key count */
   uint32_t rmi_eps_max;    /* leaves whose error bound exceeds this use the hash table; <= 255. Default 64 */
   int rmi_root;            /* GOD_ROOT_MLP, GOD_ROOT_UNTRAINED or GOD_ROOT_LINEAR */
-  int rmi_train_steps;     /* Adam fine-tuning steps after the least-squares readout; default 64 */
+  int rmi_train_steps;     /* Adam fine-tuning steps after the least-squares readout (0 = the readout
+                              alone); default 64 */
   uint32_t rmi_train_samples; /* keys sampled for root training; default 65536 */
   int tune;                /* 1 = autotune the sketch launch (cached per shape); 0 = fixed default */
 } god_params;

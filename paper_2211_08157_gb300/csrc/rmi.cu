@@ -425,7 +425,7 @@ int build_rmi(god_index* idx, cudaStream_t st) {
   DBuf<RmiRoot> d_root;
   GOD_TRY(d_root.alloc(1, st));
   float loss = 0.0f;
-  if (P.rmi_root == GOD_ROOT_MLP && P.rmi_train_steps > 0) {
+  if (P.rmi_root == GOD_ROOT_MLP) {   // the least-squares readout always; then rmi_train_steps Adam steps
     const uint64_t S = std::min<uint64_t>(U, std::max<uint32_t>(P.rmi_train_samples, 1));
     DBuf<float> xs, ys, theta, m1, m2, partial, gout;
     GOD_TRY(xs.alloc(S, st));
@@ -444,7 +444,7 @@ int build_rmi(god_index* idx, cudaStream_t st) {
     GOD_CK(cudaMemsetAsync(m1.p, 0, NP * sizeof(float), st));
     GOD_CK(cudaMemsetAsync(m2.p, 0, NP * sizeof(float), st));
     const float inv_n = 1.0f / (float)S;
-    const int steps = P.rmi_train_steps;
+    const int steps = P.rmi_train_steps > 0 ? P.rmi_train_steps : 0;
     // 1. exact least-squares output layer over the fixed ReLU features
     DBuf<double> gpart;
     DBuf<float> best, gbest;

@@ -45,7 +45,7 @@ struct SegArgs {
   uint32_t* sub_cnt;
 };
 
-template <typename KT, int HM, int W, bool STAGE>
+template <typename KT, int HM, int W, bool STAGE, bool X1>
 __global__ void __launch_bounds__(kSegThreads, (W <= 11 ? 6 : 3)) sketch_seg_kernel(const __grid_constant__ SegArgs a) {
   extern __shared__ __align__(16) unsigned char seg_smem[];
   constexpr int ROW = 2 * W + 1;              // keys B[W], minima C[W]; odd stride: no bank conflicts
@@ -131,8 +131,12 @@ __global__ void __launch_bounds__(kSegThreads, (W <= 11 ? 6 : 3)) sketch_seg_ker
     const uint32_t pre = min(m, (uint32_t)k - 1);
     for (uint32_t i = 0; i < pre; ++i) {
       const uint32_t c = (STAGE && staged) ? csrc[o] : s_lut[__ldg(src + o)];
-      o += s_delta[r];
-      r = r + 1 == (uint32_t)x ? 0 : r + 1;
+      if (X1) {   // weight-1 pattern: every kept base is p bytes after the last
+        o += (uint32_t)p;
+      } else {
+        o += s_delta[r];
+        r = r + 1 == (uint32_t)x ? 0 : r + 1;
+      }
       nflag |= c >> 2;
       run = c > 3 ? 0 : run + 1;
       fwd = (fwd << 2) | (c & 3u);
@@ -156,8 +160,12 @@ __global__ void __launch_bounds__(kSegThreads, (W <= 11 ? 6 : 3)) sketch_seg_ker
         uint32_t z = 0;
         if (j < nk) {
           const uint32_t c = (STAGE && staged) ? csrc[o] : s_lut[__ldg(src + o)];
-          o += s_delta[r];
-          r = r + 1 == (uint32_t)x ? 0 : r + 1;
+          if (X1) {
+            o += (uint32_t)p;
+          } else {
+            o += s_delta[r];
+            r = r + 1 == (uint32_t)x ? 0 : r + 1;
+          }
           nflag |= c >> 2;
           run = c > 3 ? 0 : run + 1;
           fwd = ((fwd << 2) | (c & 3u)) & mask;
@@ -182,8 +190,8 @@ __global__ void __launch_bounds__(kSegThreads, (W <= 11 ? 6 : 3)) sketch_seg_ker
           const KT ku = B[t + 1 < W ? t + 1 : 0];   // key of k-mer u = j - W + 1
           if (ku == Y && ku != 0 && ku != PALIN) {
             const uint32_t u = j - (W - 1);
-            uint32_t q, rr;
-            divmod_x(u, (uint32_t)x, xinv, q, rr);
+            uint32_t q = u, rr = 0;
+            if (!X1) divmod_x(u, (uint32_t)x, xinv, q, rr);
             MinRec rec;
             rec.key = (uint64_t)ku - 1;
             rec.pos = d.shift + (uint32_t)p * q + s_off[rr];
@@ -212,7 +220,10 @@ __global__ void __launch_bounds__(kSegThreads, (W <= 11 ? 6 : 3)) sketch_seg_ker
 
 template <typename KT, int HM, int W>
 int launch_seg(const SegArgs& a, cudaStream_t st) {
-  auto sketch_seg = a.job.bytes_on_host ? sketch_seg_kernel<KT, HM, W, true> : sketch_seg_kernel<KT, HM, W, false>;
+  const bool x1 = a.job.pat.x == 1;
+  auto sketch_seg = a.job.bytes_on_host
+                        ? (x1 ? sketch_seg_kernel<KT, HM, W, true, true> : sketch_seg_kernel<KT, HM, W, true, false>)
+                        : (x1 ? sketch_seg_kernel<KT, HM, W, false, true> : sketch_seg_kernel<KT, HM, W, false, false>);
   const size_t rows = ((size_t)kSegThreads * (2 * W + 1) * sizeof(KT) + 15) & ~(size_t)15;
   const size_t smem = rows + (a.job.bytes_on_host ? (size_t)(kSegThreads / 32) * kWarpBytes : 0);
   GOD_CK(cudaFuncSetAttribute(sketch_seg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
