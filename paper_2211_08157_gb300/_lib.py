@@ -21,7 +21,7 @@ LIB = os.path.join(PKG, "libgod.so")
 INCLUDE = os.path.join(ROOT, "include")
 SOURCES = ["api.cu", "scan.cu", "sketch.cu", "radix.cu", "index.cu", "rmi.cu", "seed.cu", "serve.cu", "vote.cu",
            "segment.cu", "contain.cu", "seedmatch.cu",
-           "sketch_seg.cu", "bucket.cu"]
+           "sketch_seg.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
               "-Xcompiler", "-Wall", "-I", INCLUDE]

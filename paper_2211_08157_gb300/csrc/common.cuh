@@ -227,17 +227,6 @@ extern std::atomic<int> g_graphs_on;
 int radix_sort_pairs(uint64_t* keys, uint64_t* vals, uint64_t n, int key_bits, cudaStream_t st);
 // The same with 32-bit values.
 int radix_sort_pairs32(uint64_t* keys, uint32_t* vals, uint64_t n, int key_bits, cudaStream_t st);
-// Sort of (key, value) pairs with distinct values by (key, value), for keys
-// uniform over [0, 2^key_bits) and values below 2^vbits: one bucket pass by
-// the key's top bits, then a shared-memory sort per bucket. *done is false
-// (nothing changed) when the batch is too small or (low key bits, value) does
-// not fit in 64 bits; the caller then sorts by digits. *d_err (device) is set
-// to 1 when a prefix-sum wait gave up; the caller reads it back.
-int bucket_sort_pairs(uint64_t* keys, uint64_t* vals, uint64_t n, int key_bits, int vbits, int* d_err,
-                      cudaStream_t st, bool* done);
-int bucket_sort_pairs32(uint64_t* keys, uint32_t* vals, uint64_t n, int key_bits, int vbits, int* d_err,
-                        cudaStream_t st, bool* done);
-
 // ------------------------------------------------------------------ index
 constexpr uint64_t kEmptyKey = ~0ULL;
 

@@ -182,22 +182,10 @@ int sort_and_emit(god_index* idx, StagedSketch& S, uint64_t n, cudaStream_t st, 
                S.WT, keys.p, vals.p);
   }
   S.staging.release();
-  // values (pos << 1 | z) are distinct and below 2 len + 2: a bucket pass and
-  // per-bucket shared-memory sorts when (low key bits, value) fits a word,
-  // otherwise the LSD radix sort (both give the (key, position) order)
-  int vbits = 1;
-  while (vbits < 64 && (1ull << vbits) < 2 * idx->ref_len + 2) ++vbits;
-  bool done = false;
-  DBuf<int> bk_err;
-  GOD_TRY(bk_err.alloc(1, st));
-  GOD_CK(cudaMemsetAsync(bk_err.p, 0, sizeof(int), st));
-  if constexpr (sizeof(V) == 4) {
-    GOD_TRY(bucket_sort_pairs32(keys.p, vals.p, n, 2 * idx->k, vbits, bk_err.p, st, &done));
-    if (!done) GOD_TRY(radix_sort_pairs32(keys.p, vals.p, n, 2 * idx->k, st));
-  } else {
-    GOD_TRY(bucket_sort_pairs(keys.p, vals.p, n, 2 * idx->k, vbits, bk_err.p, st, &done));
-    if (!done) GOD_TRY(radix_sort_pairs(keys.p, vals.p, n, 2 * idx->k, st));
-  }
+  if constexpr (sizeof(V) == 4)
+    GOD_TRY(radix_sort_pairs32(keys.p, vals.p, n, 2 * idx->k, st));
+  else
+    GOD_TRY(radix_sort_pairs(keys.p, vals.p, n, 2 * idx->k, st));
 
   // runs of equal keys, the filter, and the output arrays
   DBuf<uint64_t> rv, roff;
@@ -206,12 +194,9 @@ int sort_and_emit(god_index* idx, StagedSketch& S, uint64_t n, cudaStream_t st, 
   if (n) GOD_LAUNCH(run_heads, g, kThreads, 0, st, keys.p, n, idx->max_occ, rv.p);
   GOD_TRY(exclusive_scan_u64(rv.p, roff.p, n, st));
   uint64_t tot = 0;
-  int h_bk_err = 0;
   GOD_CK(cudaMemcpyAsync(&tot, roff.p + n, 8, cudaMemcpyDeviceToHost, st));
-  GOD_CK(cudaMemcpyAsync(&h_bk_err, bk_err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
   GOD_CK(cudaStreamSynchronize(st));
   GOD_TRY(scan_total_ok(tot, "index"));
-  if (h_bk_err) GOD_TRY(scan_total_ok(kScanPoison, "index sort"));
   const uint64_t U = tot >> 32, E = tot & 0xFFFFFFFFULL;
   GOD_TRY(okeys.alloc(U, st));
   GOD_TRY(ostart.alloc(U + 1, st));
