@@ -80,11 +80,59 @@ void prof_add_work(const char* name, double bytes, double units) {
   t.units += units;
 }
 
+// Work whose size is only known on the device (records a kernel emitted): the
+// count is copied to a page-locked slot on the stream and read when the
+// profile is collected, so no synchronisation is added to the pass.
+struct ProfCount {
+  const char* name;
+  cudaEvent_t e;
+  unsigned long long* slot;
+  double bytes, per, units, units_per;
+};
+static std::vector<ProfCount> g_prof_counts;
+static std::vector<unsigned long long*> g_prof_slots;   // free page-locked slots
+
+void prof_add_work_async(const char* name, const unsigned long long* d_count, double bytes, double bytes_per_count,
+                         double units, double units_per_count, cudaStream_t st) {
+  if (!g_prof_on.load(std::memory_order_relaxed)) return;
+  unsigned long long* slot = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (g_prof_slots.empty()) {
+      constexpr int kChunk = 256;
+      unsigned long long* chunk = nullptr;
+      if (cudaHostAlloc((void**)&chunk, kChunk * sizeof(unsigned long long), cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+      }
+      for (int i = 0; i < kChunk; ++i) g_prof_slots.push_back(chunk + i);
+    }
+    slot = g_prof_slots.back();
+    g_prof_slots.pop_back();
+  }
+  cudaEvent_t e = prof_event();
+  cudaMemcpyAsync(slot, d_count, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
+  cudaEventRecord(e, st);
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_prof_counts.push_back(ProfCount{name, e, slot, bytes, bytes_per_count, units, units_per_count});
+}
+
 static void prof_collect() {
   std::vector<ProfPending> pend;
+  std::vector<ProfCount> counts;
   {
     std::lock_guard<std::mutex> lk(g_prof_mu);
     pend.swap(g_prof_pending);
+    counts.swap(g_prof_counts);
+  }
+  for (auto& c : counts) {
+    cudaEventSynchronize(c.e);
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    ProfTotal& t = g_prof_tot[c.name];
+    t.bytes += c.bytes + c.per * (double)*c.slot;
+    t.units += c.units + c.units_per * (double)*c.slot;
+    g_prof_free.push_back(c.e);
+    g_prof_slots.push_back(c.slot);
   }
   for (auto& p : pend) {
     float ms = 0.0f;

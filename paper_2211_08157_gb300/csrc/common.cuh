@@ -48,6 +48,11 @@ void prof_begin(cudaStream_t st, cudaEvent_t* a);
 void prof_end(const char* name, cudaStream_t st, cudaEvent_t a);
 // Adds algorithmic bytes (and processed units) to a kernel's profile entry.
 void prof_add_work(const char* name, double bytes, double units);
+// The same, with bytes + bytes_per_count x n and units + units_per_count x n,
+// n = *d_count: a device counter copied on the stream without synchronising
+// and resolved when the profile is read.
+void prof_add_work_async(const char* name, const unsigned long long* d_count, double bytes, double bytes_per_count,
+                         double units, double units_per_count, cudaStream_t st);
 
 // Every kernel launch goes through this macro: it counts the launch, times it
 // when profiling is on, and turns a launch failure into GOD_ECUDA.
@@ -190,7 +195,11 @@ struct StagedSketch {
 };
 int run_sketch_staged(const SketchJob& job, cudaStream_t st, StagedSketch& out, const SketchTune* tune);
 // The one-thread-per-segment kernel (sketch_seg.cu): whether it takes this
-// job, and the pass itself (same records and order as the tile kernel).
+// job (seg_cnt set, every segment short, w in {10, 11, 19}), and the pass
+// itself: the same records and order as the tile kernel, one sub-tile per
+// segment (sub_cnt = the segment counts, sub_off their scan, sub_base =
+// seg_voff). The total stays on the device (sub_off[n_sub]); out.total is
+// not set.
 bool sketch_segments_ok(const SketchJob& job);
 int run_sketch_segments(const SketchJob& job, cudaStream_t st, StagedSketch& out);
 SketchTune default_sketch_tune(int k, int w);

@@ -794,7 +794,7 @@ struct SetBufs {
   DBuf<uint32_t> seg_cnt;
   DBuf<uint64_t> seg_off;
   DBuf<uint32_t> max_m;      // longest segment (set by the segment builders)
-  uint64_t n_seg = 0, n_rec = 0;
+  uint64_t n_seg = 0;
   RecSet view() const { return RecSet{pz.p, sc.p, seg_off.p, seg_cnt.p}; }
 };
 
@@ -831,38 +831,48 @@ int sketch_and_lookup(const god_index* idx, const uint8_t* d_reads, SetBufs& B, 
   job.tune = idx->params.tune;
   job.max_m = max_m;
   job.bytes_on_host = is_device_ptr(d_reads) ? 0 : 1;
+  const DeviceIndex di = device_view(idx, via);
+  const bool learned = via == 1 && di.leaves;
   StagedSketch SS;
+  if (V > 0 && sketch_segments_ok(job)) {
+    // short segments, one thread each: the record total stays on the device
+    // (pz / sc sized for V records, its bound), and the segment offsets are
+    // the pass's own sub-tile offsets
+    GOD_TRY(run_sketch_segments(job, st, SS));
+    GOD_TRY(B.pz.alloc(V, st));
+    GOD_TRY(B.sc.alloc(V, st));
+    const unsigned blocks =
+        (unsigned)std::min<uint64_t>(((SS.n_sub + 31) / 32 * 32 + kT - 1) / kT, (uint64_t)num_sms() * 16);
+    if (learned)
+      GOD_LAUNCH(compact_lookup_seg<1>, blocks, kT, 0, st, SS.staging.p, SS.sub_cnt.p, SS.sub_off.p, SS.n_sub,
+                 SS.sub_base, di, B.pz.p, B.sc.p);
+    else
+      GOD_LAUNCH(compact_lookup_seg<0>, blocks, kT, 0, st, SS.staging.p, SS.sub_cnt.p, SS.sub_off.p, SS.n_sub,
+                 SS.sub_base, di, B.pz.p, B.sc.p);
+    // algorithmic bytes: record read 16, position word 4, result 8, one table
+    // slot 8 and the key's two offsets 8
+    prof_add_work_async(learned ? "compact_lookup_seg<1>" : "compact_lookup_seg<0>",
+                        reinterpret_cast<const unsigned long long*>(SS.sub_off.p + SS.n_sub), 0.0, 44.0, 0.0, 1.0,
+                        st);
+    B.seg_off.st = st;
+    B.seg_off.n = SS.sub_off.n;
+    B.seg_off.p = SS.sub_off.take();
+    return GOD_OK;
+  }
   GOD_TRY(run_sketch_staged(job, st, SS, nullptr));
-  B.n_rec = SS.total;
   GOD_TRY(B.pz.alloc(SS.total, st));
   GOD_TRY(B.sc.alloc(SS.total, st));
   if (SS.total) {
-    const DeviceIndex di = device_view(idx, via);
-    const bool learned = via == 1 && di.leaves;
-    if (SS.sub_base) {
-      const unsigned blocks =
-          (unsigned)std::min<uint64_t>(((SS.n_sub + 31) / 32 * 32 + kT - 1) / kT, (uint64_t)num_sms() * 16);
-      if (learned)
-        GOD_LAUNCH(compact_lookup_seg<1>, blocks, kT, 0, st, SS.staging.p, SS.sub_cnt.p, SS.sub_off.p, SS.n_sub,
-                   SS.sub_base, di, B.pz.p, B.sc.p);
-      else
-        GOD_LAUNCH(compact_lookup_seg<0>, blocks, kT, 0, st, SS.staging.p, SS.sub_cnt.p, SS.sub_off.p, SS.n_sub,
-                   SS.sub_base, di, B.pz.p, B.sc.p);
-    } else {
-      const unsigned blocks =
-          (unsigned)std::min<uint64_t>((SS.n_sub * 32 + kT - 1) / kT, (uint64_t)num_sms() * 16);
-      if (learned)
-        GOD_LAUNCH(compact_lookup<1>, blocks, kT, 0, st, SS.staging.p, SS.sub_cnt.p, SS.sub_off.p, SS.n_sub, SS.WT,
-                   di, B.pz.p, B.sc.p);
-      else
-        GOD_LAUNCH(compact_lookup<0>, blocks, kT, 0, st, SS.staging.p, SS.sub_cnt.p, SS.sub_off.p, SS.n_sub, SS.WT,
-                   di, B.pz.p, B.sc.p);
-    }
+    const unsigned blocks = (unsigned)std::min<uint64_t>((SS.n_sub * 32 + kT - 1) / kT, (uint64_t)num_sms() * 16);
+    if (learned)
+      GOD_LAUNCH(compact_lookup<1>, blocks, kT, 0, st, SS.staging.p, SS.sub_cnt.p, SS.sub_off.p, SS.n_sub, SS.WT, di,
+                 B.pz.p, B.sc.p);
+    else
+      GOD_LAUNCH(compact_lookup<0>, blocks, kT, 0, st, SS.staging.p, SS.sub_cnt.p, SS.sub_off.p, SS.n_sub, SS.WT, di,
+                 B.pz.p, B.sc.p);
     // algorithmic bytes: record read 16, position word 4, result 8, one table
     // slot 8 and the key's two offsets 8
-    prof_add_work(SS.sub_base ? (learned ? "compact_lookup_seg<1>" : "compact_lookup_seg<0>")
-                              : (learned ? "compact_lookup<1>" : "compact_lookup<0>"),
-                  44.0 * (double)SS.total, (double)SS.total);
+    prof_add_work(learned ? "compact_lookup<1>" : "compact_lookup<0>", 44.0 * (double)SS.total, (double)SS.total);
   }
   GOD_TRY(B.seg_off.alloc(B.n_seg + 1, st));
   GOD_TRY(exclusive_scan_u32(B.seg_cnt.p, B.seg_off.p, B.n_seg, st));

@@ -955,7 +955,6 @@ int autotune(const SketchJob& job, cudaStream_t st, SketchTune* best) {
 }  // namespace
 
 int run_sketch_staged(const SketchJob& job, cudaStream_t st, StagedSketch& o, const SketchTune* tune) {
-  if (!tune && job.V > 0 && sketch_segments_ok(job)) return run_sketch_segments(job, st, o);
   SketchTune tn = clamp_tune(tune ? *tune : default_sketch_tune(job.k, job.w), job.k, job.w);
   o.total = 0;
   o.WT = tn.tile;

@@ -268,13 +268,10 @@ int run_sketch_segments(const SketchJob& job, cudaStream_t st, StagedSketch& o) 
   else if (job.w == 11) GOD_TRY(launch_seg_w<11>(a, st));
   else GOD_TRY(launch_seg_w<19>(a, st));
   GOD_TRY(exclusive_scan_u32(o.sub_cnt.p, o.sub_off.p, job.n_seg, st));
-  uint64_t tot = 0;
-  GOD_CK(cudaMemcpyAsync(&tot, o.sub_off.p + job.n_seg, 8, cudaMemcpyDeviceToHost, st));
-  GOD_CK(cudaStreamSynchronize(st));
-  GOD_TRY(scan_total_ok(tot, "sketch"));
-  o.total = tot;
-  // algorithmic bytes: every patterned base read once, every record written once
-  prof_add_work("sketch_seg", (double)(job.V - job.n_seg) + 16.0 * (double)tot, (double)(job.V - job.n_seg));
+  // algorithmic bytes: every patterned base read once, every record written
+  // once (the record count is read when the profile is)
+  prof_add_work_async("sketch_seg", reinterpret_cast<const unsigned long long*>(o.sub_off.p + job.n_seg),
+                      (double)(job.V - job.n_seg), 16.0, (double)(job.V - job.n_seg), 0.0, st);
   return GOD_OK;
 }
 
