@@ -414,6 +414,11 @@ int god_server_wait(god_server *s, uint64_t request_id, int timeout_ms, god_anch
 typedef struct {
   uint64_t submitted, completed, batches, max_inflight_batches, merged_requests;
   uint64_t rejected;       /* requests larger than the memory budget */
+  /* Seconds the worker threads spent, summed over slots: copying request
+   * bytes into page-locked staging; allocating page-locked memory (staging
+   * growth, result buffers); the device pass (input copy, seeding, with its
+   * own synchronisations); cutting the result and copying it back. */
+  double gather_s, pin_alloc_s, device_s, copy_back_s;
 } god_server_stats;
 
 int god_server_get_stats(god_server *s, god_server_stats *st);

@@ -115,7 +115,9 @@ class ServerConfig(C.Structure):
 
 class ServerStats(C.Structure):
     _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("batches", C.c_uint64),
-                ("max_inflight_batches", C.c_uint64), ("merged_requests", C.c_uint64), ("rejected", C.c_uint64)]
+                ("max_inflight_batches", C.c_uint64), ("merged_requests", C.c_uint64), ("rejected", C.c_uint64),
+                ("gather_s", C.c_double), ("pin_alloc_s", C.c_double), ("device_s", C.c_double),
+                ("copy_back_s", C.c_double)]
 
 
 # name -> (restype, argtypes); every symbol declared in include/god.h

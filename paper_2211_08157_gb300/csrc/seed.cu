@@ -351,9 +351,25 @@ __global__ void __launch_bounds__(kT) fill_sort_small(RecSets sets, const uint32
         const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
         if (lane >= d) incl += y;
       }
-      const uint32_t excl = base + incl - c;
-      for (uint32_t e = 0; e < c; ++e) B[excl + e] = anchor_key(__ldg(ent + start + e), pos, z);
-      base += __shfl_sync(0xffffffffu, incl, 31);
+      // the 32 records' entries expanded by the whole warp (a lane finds the
+      // record of entry q by a binary search over the lanes' exclusive counts)
+      const uint32_t ex = incl - c;
+      const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
+      for (uint32_t q0 = 0; q0 < tot; q0 += 32) {
+        const uint32_t q = q0 + lane;
+        int L = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+          const uint32_t e = __shfl_sync(0xffffffffu, ex, L + step);
+          if (e <= q) L += step;
+        }
+        const uint32_t eL = __shfl_sync(0xffffffffu, ex, L);
+        const uint32_t sL = __shfl_sync(0xffffffffu, start, L);
+        const uint32_t pL = __shfl_sync(0xffffffffu, pos, L);
+        const uint32_t zL = __shfl_sync(0xffffffffu, z, L);
+        if (q < tot) B[base + q] = anchor_key(__ldg(ent + sL + (q - eL)), pL, zL);
+      }
+      base += tot;
     }
     __syncwarp();
     for (uint32_t e = lane; e < n; e += 32) {

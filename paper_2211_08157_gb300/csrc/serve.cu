@@ -13,10 +13,12 @@
 // concurrently, so requests that arrive while others are on the GPU overlap
 // with them. Integer results do not depend on how requests were merged.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <map>
 #include <mutex>
 #include <thread>
 #include <unordered_map>
@@ -45,61 +47,92 @@ struct Request {
   uint64_t n_result = 0;
 };
 
+// Page-locked host memory cache shared by every server of the process.
+// Pinning fresh memory (cudaMallocHost) runs at a few GB/s and holds the
+// driver's lock meanwhile, stalling the other slots' CUDA calls; measured on
+// the serving stream it took a third of the slots' time. So buffers go back
+// to this cache rather than to the system, and later batches (and later
+// servers) take them again. Blocks are sized with headroom so that they fit
+// more batches; a block is taken only for needs of at least a quarter of its
+// size; free blocks beyond kPinCacheCap bytes are released.
+constexpr uint64_t kPinCacheCap = 16ull << 30;
+struct PinCache {
+  std::mutex mu;
+  std::multimap<uint64_t, void*> free_blocks;   // size -> block
+  uint64_t cached = 0;
+};
+PinCache& pin_cache() {
+  static PinCache* c = new PinCache();   // never destroyed: slices may outlive static destruction order
+  return *c;
+}
+
+void* pinned_take(uint64_t need, uint64_t* got) {
+  PinCache& C = pin_cache();
+  {
+    std::lock_guard<std::mutex> lk(C.mu);
+    auto it = C.free_blocks.lower_bound(need);
+    if (it != C.free_blocks.end() && it->first / 4 <= need) {
+      void* p = it->second;
+      *got = it->first;
+      C.cached -= it->first;
+      C.free_blocks.erase(it);
+      return p;
+    }
+  }
+  // headroom: the next power of two at or above 1.25 x need (at least 4 MiB)
+  uint64_t sz = 4ull << 20;
+  while (sz < need + need / 4) sz <<= 1;
+  void* p = nullptr;
+  if (cudaMallocHost(&p, sz) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  *got = sz;
+  return p;
+}
+
+void pinned_give(void* p, uint64_t size) {
+  if (!p) return;
+  PinCache& C = pin_cache();
+  {
+    std::lock_guard<std::mutex> lk(C.mu);
+    if (C.cached + size <= kPinCacheCap) {
+      C.free_blocks.emplace(size, p);
+      C.cached += size;
+      return;
+    }
+  }
+  cudaFreeHost(p);
+}
+
 // Page-locked buffer holding one batch's anchors; every request of the batch
 // gets its result as a slice of it (no per-request copy), and the buffer goes
-// back to the server's pool when the last slice has been freed (god_free).
-struct ResultPool;
+// back to the cache when the last slice has been freed (god_free), also after
+// the server is gone.
 struct Arena {
   god_anchor* p = nullptr;
-  uint64_t cap = 0;
-  int refs = 0;                 // live slices, guarded by pool->mu
-  ResultPool* pool = nullptr;   // null once the server is gone
-};
-struct ResultPool {
-  std::mutex mu;
-  std::vector<Arena*> free_list;
-  std::vector<Arena*> all;
+  uint64_t bytes = 0;
+  std::atomic<int> refs{0};     // live slices
 };
 
 void arena_release(void* ctx) {
   Arena* a = static_cast<Arena*>(ctx);
-  ResultPool* pool = a->pool;
-  if (!pool) {   // the server is gone: the last slice frees the buffer
-    if (--a->refs == 0) {
-      cudaFreeHost(a->p);
-      delete a;
-    }
-    return;
+  if (a->refs.fetch_sub(1) == 1) {
+    pinned_give(a->p, a->bytes);
+    delete a;
   }
-  std::lock_guard<std::mutex> lk(pool->mu);
-  if (--a->refs == 0) pool->free_list.push_back(a);
 }
 
-// A free arena of at least `need` anchors (the smallest that fits), or a new one.
-Arena* arena_take(ResultPool* pool, uint64_t need) {
-  {
-    std::lock_guard<std::mutex> lk(pool->mu);
-    size_t best = pool->free_list.size();
-    for (size_t i = 0; i < pool->free_list.size(); ++i)
-      if (pool->free_list[i]->cap >= need && (best == pool->free_list.size() ||
-                                                pool->free_list[i]->cap < pool->free_list[best]->cap))
-        best = i;
-    if (best < pool->free_list.size()) {
-      Arena* a = pool->free_list[best];
-      pool->free_list.erase(pool->free_list.begin() + best);
-      return a;
-    }
-  }
+// A buffer for `need` anchors.
+Arena* arena_take(uint64_t need) {
   Arena* a = new Arena();
-  a->cap = std::max<uint64_t>(need, 1ull << 20);
-  if (cudaMallocHost(&a->p, a->cap * sizeof(god_anchor)) != cudaSuccess) {
-    cudaGetLastError();
+  uint64_t got = 0;
+  a->p = static_cast<god_anchor*>(pinned_take(std::max<uint64_t>(need, 1) * sizeof(god_anchor), &got));
+  if (!a->p) {
     delete a;
     return nullptr;
   }
-  a->pool = pool;
-  std::lock_guard<std::mutex> lk(pool->mu);
-  pool->all.push_back(a);
+  a->bytes = got;
   return a;
 }
 
@@ -195,7 +228,6 @@ struct god_server {
   uint64_t inflight = 0;
   bool stop = false;
   god_server_stats st{};
-  ResultPool pool;
 };
 
 namespace {
@@ -206,7 +238,7 @@ void worker_main(god_server* S, int slot) {
   cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking);
   uint8_t* h_reads = nullptr;
   uint64_t* h_offs = nullptr;
-  size_t cap_reads = 0, cap_offs = 0;
+  uint64_t cap_reads = 0, cap_offs = 0;   // bytes
   (void)slot;
   while (true) {
     std::vector<Request*> batch;
@@ -264,18 +296,25 @@ void worker_main(god_server* S, int slot) {
       if (S->stop && batch.empty()) break;
     }
     // ---- concatenate the batch into pinned staging
+    auto secs = [](Clock::time_point a, Clock::time_point b) { return std::chrono::duration<double>(b - a).count(); };
+    double t_alloc = 0.0;
+    const auto t0 = Clock::now();
     uint64_t bases = 0, n = 0;
     for (Request* r : batch) { bases += r->bases; n += r->n; }
     int rc = GOD_OK;
     if (bases > cap_reads) {
-      if (h_reads) cudaFreeHost(h_reads);
-      cap_reads = std::max<uint64_t>(bases, 1 << 20);
-      if (cudaMallocHost(&h_reads, cap_reads) != cudaSuccess) { h_reads = nullptr; cap_reads = 0; rc = GOD_ENOMEM; }
+      const auto a0 = Clock::now();
+      pinned_give(h_reads, cap_reads);
+      h_reads = static_cast<uint8_t*>(pinned_take(bases, &cap_reads));
+      if (!h_reads) { cap_reads = 0; rc = GOD_ENOMEM; }
+      t_alloc += secs(a0, Clock::now());
     }
-    if (rc == GOD_OK && n + 1 > cap_offs) {
-      if (h_offs) cudaFreeHost(h_offs);
-      cap_offs = std::max<uint64_t>(n + 1, 1 << 16);
-      if (cudaMallocHost(&h_offs, cap_offs * 8) != cudaSuccess) { h_offs = nullptr; cap_offs = 0; rc = GOD_ENOMEM; }
+    if (rc == GOD_OK && (n + 1) * 8 > cap_offs) {
+      const auto a0 = Clock::now();
+      pinned_give(h_offs, cap_offs);
+      h_offs = static_cast<uint64_t*>(pinned_take((n + 1) * 8, &cap_offs));
+      if (!h_offs) { cap_offs = 0; rc = GOD_ENOMEM; }
+      t_alloc += secs(a0, Clock::now());
     }
     std::vector<uint64_t> first_read;
     if (rc == GOD_OK) {
@@ -291,6 +330,7 @@ void worker_main(god_server* S, int slot) {
       h_offs[ro] = bo;
       gather_bytes(parts, h_reads);
     }
+    const auto t1 = Clock::now();
     // ---- device pass
     god::DBuf<uint8_t> d_reads;
     god::DBuf<uint64_t> d_offs;
@@ -307,11 +347,14 @@ void worker_main(god_server* S, int slot) {
       rc = god::seed_device(S->idx, d_reads.p, d_offs.p, (uint32_t)n, bases, o, stream, &d_out, &total, nullptr, 0,
                             true);
     }
+    const auto t2 = Clock::now();
     Arena* arena = nullptr;
     if (rc == GOD_OK && total) {
-      arena = arena_take(&S->pool, total);
+      arena = arena_take(total);
       if (!arena) rc = GOD_ENOMEM;
     }
+    const auto t3 = Clock::now();
+    t_alloc += secs(t2, t3);
     // request boundaries and per-request read ids on the device, so the
     // split below is one copy per request
     const uint32_t m = (uint32_t)batch.size();
@@ -335,6 +378,7 @@ void worker_main(god_server* S, int slot) {
     d_reads.release();
     d_offs.release();
     if (cudaStreamSynchronize(stream) != cudaSuccess && rc == GOD_OK) rc = GOD_ECUDA;
+    const auto t4 = Clock::now();
     // ---- split per request: slices of the arena (an empty result gets a
     // small host array of its own, so that every result pointer is distinct)
     int slices = 0;
@@ -355,9 +399,12 @@ void worker_main(god_server* S, int slot) {
       r->merged = batch.size() > 1;
     }
     if (arena) {
-      std::lock_guard<std::mutex> lk(S->pool.mu);
-      arena->refs += slices;
-      if (arena->refs == 0) S->pool.free_list.push_back(arena);
+      if (slices == 0) {
+        pinned_give(arena->p, arena->bytes);
+        delete arena;
+      } else {
+        arena->refs.store(slices);
+      }
     }
     {
       std::lock_guard<std::mutex> lk(S->mu);
@@ -369,12 +416,16 @@ void worker_main(god_server* S, int slot) {
       }
       S->mem_in_use -= est;
       S->inflight--;
+      S->st.gather_s += secs(t0, t1) - (t_alloc - secs(t2, t3));
+      S->st.pin_alloc_s += t_alloc;
+      S->st.device_s += secs(t1, t2);
+      S->st.copy_back_s += secs(t3, t4);
     }
     S->cv_done.notify_all();
     S->cv_work.notify_all();
   }
-  if (h_reads) cudaFreeHost(h_reads);
-  if (h_offs) cudaFreeHost(h_offs);
+  pinned_give(h_reads, cap_reads);
+  pinned_give(h_offs, cap_offs);
   cudaStreamDestroy(stream);
 }
 
@@ -490,18 +541,7 @@ int god_server_destroy(god_server* S) {
     else if (kv.second->result) free(kv.second->result);
     delete kv.second;
   }
-  {
-    // arenas with live slices outlive the server; the last slice frees them
-    std::lock_guard<std::mutex> lk(S->pool.mu);
-    for (Arena* a : S->pool.all) {
-      if (a->refs == 0) {
-        cudaFreeHost(a->p);
-        delete a;
-      } else {
-        a->pool = nullptr;
-      }
-    }
-  }
+  // arenas with live slices outlive the server; the last slice returns them
   delete S;
   return GOD_OK;
 }
