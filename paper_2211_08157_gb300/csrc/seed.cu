@@ -31,6 +31,8 @@ namespace {
 constexpr int kT = 256;
 constexpr uint32_t kSrcPA = 0, kSrcFB = 1, kSrcP2 = 2;
 constexpr int kSmallCap = 128;          // anchors per read for the warp path
+constexpr int kMedThreads = 128;
+constexpr int kMedCap = 1024;           // anchors per read for the medium CTA path
 constexpr int kLargeThreads = 256;
 constexpr int kLargeCap = 4096;         // anchors sorted in shared memory at once
 constexpr int kLargeRounds = kLargeCap / kLargeThreads;
@@ -217,15 +219,36 @@ __global__ void count_anchors_list(const uint32_t* __restrict__ list, uint32_t n
 
 // Reads by anchor-list length: tiny (thread path), small (warp path), large
 // (CTA path). Lists are unordered; every read writes its own output range.
+// counts: [tiny, small, medium, large, huge reads, chunks of the huge reads
+// (kLargeCap anchors each), most chunks of one read].
 __global__ void classify_reads(uint32_t n, const uint64_t* __restrict__ read_off, uint32_t* __restrict__ tiny,
-                               uint32_t* __restrict__ small, uint32_t* __restrict__ large,
-                               uint32_t* __restrict__ huge, unsigned long long* __restrict__ counts) {
+                               uint32_t* __restrict__ small, uint32_t* __restrict__ medium,
+                               uint32_t* __restrict__ large, uint32_t* __restrict__ huge,
+                               unsigned long long* __restrict__ counts) {
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t c = read_off[i + 1] - read_off[i];
     warp_append(c > 0 && c <= kTinyCap, (uint32_t)i, tiny, counts + 0);
     warp_append(c > kTinyCap && c <= kSmallCap, (uint32_t)i, small, counts + 1);
-    warp_append(c > kSmallCap && c <= kLargeCap, (uint32_t)i, large, counts + 2);
-    warp_append(c > kLargeCap, (uint32_t)i, huge, counts + 3);
+    warp_append(c > kSmallCap && c <= kMedCap, (uint32_t)i, medium, counts + 2);
+    warp_append(c > kMedCap && c <= kLargeCap, (uint32_t)i, large, counts + 3);
+    warp_append(c > kLargeCap, (uint32_t)i, huge, counts + 4);
+    if (c > kLargeCap) {
+      const unsigned long long ch = (c + kLargeCap - 1) / kLargeCap;
+      atomicAdd(counts + 5, ch);
+      atomicMax(counts + 6, ch);
+    }
+  }
+}
+
+// One task per kLargeCap-anchor tile of every huge read: (huge-list index <<
+// 32) | tile. The chunk sorts and every merge level take the same tiles.
+__global__ void huge_tasks(const uint32_t* __restrict__ huge, uint32_t n_huge, const uint64_t* __restrict__ read_off,
+                           uint64_t* __restrict__ tasks, unsigned long long* __restrict__ ctr) {
+  for (uint32_t li = blockIdx.x * blockDim.x + threadIdx.x; li < n_huge; li += gridDim.x * blockDim.x) {
+    const uint32_t i = huge[li];
+    const uint64_t ch = (read_off[i + 1] - read_off[i] + kLargeCap - 1) / kLargeCap;
+    const unsigned long long b = atomicAdd(ctr, ch);
+    for (uint64_t c = 0; c < ch; ++c) tasks[b + c] = ((uint64_t)li << 32) | c;
   }
 }
 
@@ -456,6 +479,67 @@ __device__ void bitonic_sort_smem(uint64_t* s, uint32_t n_pad) {
   }
 }
 
+// Medium anchor lists (kSmallCap < n <= kMedCap; short reads on repeat-rich
+// references): a 128-thread CTA per read, the keys in 8 KB of shared memory
+// (16 CTAs fit an SM, where the 256-thread large path with its 74 KB fit 3 and
+// spent its time waiting at barriers), entries expanded by all threads (a
+// thread finds the record of entry q by a binary search over the records'
+// exclusive counts, so one repeat key with many entries does not leave one
+// thread loading them all), a bitonic network over the padded list.
+__global__ void __launch_bounds__(kMedThreads) fill_sort_medium(RecSets sets, const uint32_t* __restrict__ src,
+                                                                const uint32_t* __restrict__ seed_seg,
+                                                                const uint64_t* __restrict__ read_off,
+                                                                const uint32_t* __restrict__ list, uint32_t nl,
+                                                                const uint64_t* __restrict__ ent,
+                                                                god_anchor* __restrict__ out) {
+  __shared__ uint64_t s[kMedCap];
+  __shared__ uint32_t s_ex[kMedThreads], s_start[kMedThreads], s_pz[kMedThreads];
+  __shared__ uint32_t warp_buf[kMedThreads / 32 + 1];
+  for (uint32_t li = blockIdx.x; li < nl; li += gridDim.x) {
+    const uint32_t i = list[li];
+    const uint64_t off = read_off[i];
+    const uint32_t n = (uint32_t)(read_off[i + 1] - off);
+    const RecSet S = pick_set(sets, src[i]);
+    const uint32_t g = seed_seg[i];
+    const uint64_t beg = S.seg_off[g];
+    const uint32_t cnt = S.seg_cnt[g];
+    uint32_t base = 0;
+    for (uint32_t r0 = 0; r0 < cnt; r0 += kMedThreads) {
+      const uint32_t r = r0 + threadIdx.x;
+      uint32_t c = 0, start = 0, pzv = 0;
+      if (r < cnt) {
+        const uint64_t sc = S.sc[beg + r];
+        c = (uint32_t)(sc >> 32);
+        start = (uint32_t)sc;
+        if (c) pzv = S.pz[beg + r];
+      }
+      uint32_t tot;
+      const uint32_t ex = block_excl_scan_u32(c, &tot, warp_buf);
+      s_ex[threadIdx.x] = ex;
+      s_start[threadIdx.x] = start;
+      s_pz[threadIdx.x] = pzv;
+      __syncthreads();
+      for (uint32_t q = threadIdx.x; q < tot; q += kMedThreads) {
+        uint32_t j = 0;   // last record with s_ex[j] <= q
+#pragma unroll
+        for (uint32_t step = kMedThreads / 2; step > 0; step >>= 1)
+          if (s_ex[j + step] <= q) j += step;
+        const uint32_t pj = s_pz[j];
+        s[base + q] = anchor_key(__ldg(ent + s_start[j] + (q - s_ex[j])), pj >> 1, pj & 1u);
+      }
+      __syncthreads();
+      base += tot;
+    }
+    uint32_t n_pad = 1;
+    while (n_pad < n) n_pad <<= 1;
+    for (uint32_t q = n + threadIdx.x; q < n_pad; q += kMedThreads) s[q] = ~0ULL;
+    __syncthreads();
+    bitonic_sort_smem(s, n_pad);
+    for (uint32_t q = threadIdx.x; q < n; q += kMedThreads) store_anchor(out + off + q, i, s[q]);
+    __syncthreads();
+  }
+}
+
 // Sorted keys of s[0, n) (n <= kLargeCap): a bitonic network for up to 1024
 // keys (padded to a power of two with ~0), the radix sort past that. Returns
 // the buffer holding the result (s or t).
@@ -573,30 +657,17 @@ __device__ void key_field_bits(const uint64_t* s, uint32_t n, int* lo_bits, int*
   __syncthreads();
 }
 
-// CTA merge of sorted a[0, na) and b[0, nb) into o (merge path per thread).
-__device__ void cta_merge(const uint64_t* a, uint64_t na, const uint64_t* b, uint64_t nb, uint64_t* o) {
-  constexpr int IPT = 8;
-  const uint64_t total = na + nb;
-  for (uint64_t d0 = (uint64_t)threadIdx.x * IPT; d0 < total; d0 += (uint64_t)blockDim.x * IPT) {
-    uint64_t lo = d0 > nb ? d0 - nb : 0, hi = d0 < na ? d0 : na;
-    while (lo < hi) {
-      const uint64_t mid = (lo + hi) >> 1;
-      if (a[mid] <= b[d0 - 1 - mid]) lo = mid + 1; else hi = mid;
-    }
-    uint64_t i = lo, j = d0 - lo;
-    for (int t = 0; t < IPT && d0 + t < total; ++t) {
-      if (j >= nb || (i < na && a[i] <= b[j])) o[d0 + t] = a[i++];
-      else o[d0 + t] = b[j++];
-    }
-  }
-}
-
-// CTAs take reads from a shared counter, the lists past kLargeCap anchors
-// (chunked, the longest work) first.
+// CTAs take work from a shared counter: first the kLargeCap-anchor chunks of
+// the huge reads (each filled, sorted and written to its read's first merge
+// buffer in tmp, at twice the read's anchor offset), then the large reads
+// (filled, sorted and stored whole). Spreading a huge read's chunks over CTAs
+// matters: sorted by one CTA, a 90 kb read with 24,000 anchors held the whole
+// launch on one SM while the others idled (71 % of SM cycles idle).
 __global__ void __launch_bounds__(kLargeThreads) fill_sort_large(RecSets sets, const uint32_t* __restrict__ src,
                                                                  const uint32_t* __restrict__ seed_seg,
                                                                  const uint64_t* __restrict__ read_off,
-                                                                 const uint32_t* __restrict__ huge, uint32_t n_huge,
+                                                                 const uint32_t* __restrict__ huge,
+                                                                 const uint64_t* __restrict__ tasks, uint32_t n_tasks,
                                                                  const uint32_t* __restrict__ large, uint32_t n_large,
                                                                  const uint64_t* __restrict__ ent,
                                                                  god_anchor* __restrict__ out, uint64_t* tmp,
@@ -607,53 +678,79 @@ __global__ void __launch_bounds__(kLargeThreads) fill_sort_large(RecSets sets, c
   uint32_t* dstart = whist + (kLargeThreads / 32) * 256;
   __shared__ uint32_t warp_buf[kLargeThreads / 32 + 1];
   __shared__ uint32_t s_li;
-  const uint32_t nl = n_huge + n_large;
+  const uint32_t nl = n_tasks + n_large;
   while (true) {
     if (threadIdx.x == 0) s_li = atomicAdd(queue, 1u);
     __syncthreads();
     const uint32_t li = s_li;
     __syncthreads();
     if (li >= nl) break;
-    const uint32_t i = li < n_huge ? huge[li] : large[li - n_huge];
+    const bool chunk = li < n_tasks;
+    const uint64_t task = chunk ? tasks[li] : 0;
+    const uint32_t i = chunk ? huge[task >> 32] : large[li - n_tasks];
     const uint64_t off = read_off[i];
     const uint64_t n = read_off[i + 1] - off;
     const RecSet S = pick_set(sets, src[i]);
     const uint32_t g = seed_seg[i];
     const uint64_t beg = S.seg_off[g];
     const uint32_t cnt = S.seg_cnt[g];
-    if (n <= kLargeCap) {
-      fill_range(S, beg, cnt, ent, 0, n, sk, warp_buf);
-      __syncthreads();
-      const uint64_t* srt = cta_sort_keys(sk, sb, (uint32_t)n, whist, dstart, warp_buf);
-      for (uint32_t q = threadIdx.x; q < n; q += blockDim.x) store_anchor(out + off + q, i, srt[q]);
-      __syncthreads();
-      continue;
-    }
-    // long list: sorted runs of kLargeCap in tmp, then merge passes (ping-pong)
-    uint64_t* t0 = tmp + 2 * off;
-    uint64_t* t1 = t0 + n;
-    for (uint64_t c0 = 0; c0 < n; c0 += kLargeCap) {
-      const uint64_t c1 = std::min<uint64_t>(n, c0 + kLargeCap);
-      const uint32_t m = (uint32_t)(c1 - c0);
-      fill_range(S, beg, cnt, ent, c0, c1, sk, warp_buf);
-      __syncthreads();
-      const uint64_t* srt = cta_sort_keys(sk, sb, m, whist, dstart, warp_buf);
-      for (uint32_t q = threadIdx.x; q < m; q += blockDim.x) t0[c0 + q] = srt[q];
-      __syncthreads();
-    }
-    uint64_t* a = t0;
-    uint64_t* b = t1;
-    for (uint64_t run = kLargeCap; run < n; run <<= 1) {
-      for (uint64_t j = 0; j < n; j += 2 * run) {
-        const uint64_t na = std::min<uint64_t>(run, n - j);
-        const uint64_t nb = j + run < n ? std::min<uint64_t>(run, n - j - run) : 0;
-        cta_merge(a + j, na, a + j + na, nb, b + j);
-      }
-      __syncthreads();
-      uint64_t* t = a; a = b; b = t;
-    }
-    for (uint64_t q = threadIdx.x; q < n; q += blockDim.x) store_anchor(out + off + q, i, a[q]);
+    const uint64_t c0 = chunk ? (task & 0xFFFFFFFFull) * kLargeCap : 0;
+    const uint32_t m = (uint32_t)std::min<uint64_t>(n - c0, kLargeCap);
+    fill_range(S, beg, cnt, ent, c0, c0 + m, sk, warp_buf);
     __syncthreads();
+    const uint64_t* srt = cta_sort_keys(sk, sb, m, whist, dstart, warp_buf);
+    if (chunk) {
+      uint64_t* t0 = tmp + 2 * off;
+      for (uint32_t q = threadIdx.x; q < m; q += blockDim.x) t0[c0 + q] = srt[q];
+    } else {
+      for (uint32_t q = threadIdx.x; q < m; q += blockDim.x) store_anchor(out + off + q, i, srt[q]);
+    }
+    __syncthreads();
+  }
+}
+
+// Merge levels of the huge reads: level L (1, 2, ...) merges pairs of sorted
+// runs of kLargeCap << (L - 1) keys from one of the read's two buffers in tmp
+// into the other; a read whose chunks are all merged at this level writes its
+// anchors out instead. One CTA per output tile of kLargeCap keys (tiles never
+// straddle a pair); each thread finds its start on the merge path by a binary
+// search and merges kMergeIpt keys.
+constexpr int kMergeIpt = 8;
+__global__ void __launch_bounds__(kLargeThreads) merge_huge_level(const uint32_t* __restrict__ huge,
+                                                                  const uint64_t* __restrict__ tasks, uint32_t n_tasks,
+                                                                  const uint64_t* __restrict__ read_off, uint64_t* tmp,
+                                                                  int level, god_anchor* __restrict__ out) {
+  const uint64_t R = (uint64_t)kLargeCap << (level - 1);
+  for (uint32_t t = blockIdx.x; t < n_tasks; t += gridDim.x) {
+    const uint64_t task = tasks[t];
+    const uint32_t i = huge[task >> 32];
+    const uint64_t off = read_off[i];
+    const uint64_t n = read_off[i + 1] - off;
+    if (n <= R) continue;                                    // finished at an earlier level
+    const bool last = n <= 2 * R;
+    const uint64_t* A = tmp + 2 * off + ((level - 1) & 1 ? n : 0);
+    uint64_t* D = tmp + 2 * off + ((level - 1) & 1 ? 0 : n);
+    const uint64_t t0 = (task & 0xFFFFFFFFull) * kLargeCap;  // first output of the tile
+    const uint64_t j = t0 / (2 * R) * (2 * R);               // its pair
+    const uint64_t na = std::min<uint64_t>(R, n - j);
+    const uint64_t nb = j + R < n ? std::min<uint64_t>(R, n - j - R) : 0;
+    const uint64_t* a = A + j;
+    const uint64_t* b = a + na;
+    const uint64_t d_end = std::min<uint64_t>(t0 - j + kLargeCap, na + nb);
+    for (uint64_t d0 = t0 - j + (uint64_t)threadIdx.x * kMergeIpt; d0 < d_end;
+         d0 += (uint64_t)blockDim.x * kMergeIpt) {
+      uint64_t lo = d0 > nb ? d0 - nb : 0, hi = d0 < na ? d0 : na;
+      while (lo < hi) {
+        const uint64_t mid = (lo + hi) >> 1;
+        if (a[mid] <= b[d0 - 1 - mid]) lo = mid + 1; else hi = mid;
+      }
+      uint64_t x = lo, y = d0 - lo;
+      for (int u = 0; u < kMergeIpt && d0 + u < d_end; ++u) {
+        const uint64_t key = (y >= nb || (x < na && a[x] <= b[y])) ? a[x++] : b[y++];
+        if (last) store_anchor(out + off + j + d0 + u, i, key);
+        else D[j + d0 + u] = key;
+      }
+    }
   }
 }
 
@@ -922,14 +1019,16 @@ int seed_device(const god_index* idx, const uint8_t* d_reads, const uint64_t* d_
     if (c < cap) cap = (uint32_t)c;
   }
 
-  // small per-call state: error flag + 5 list counters in one buffer
+  // small per-call state: error flag, list counters and work queues in one buffer
+  constexpr int kCtl = 12;
   DBuf<unsigned long long> ctl;
-  GOD_TRY(ctl.alloc(8, st));
-  GOD_CK(cudaMemsetAsync(ctl.p, 0, 8 * sizeof(unsigned long long), st));
+  GOD_TRY(ctl.alloc(kCtl, st));
+  GOD_CK(cudaMemsetAsync(ctl.p, 0, kCtl * sizeof(unsigned long long), st));
   int* err = reinterpret_cast<int*>(ctl.p);
   unsigned long long* pa_counts = ctl.p + 1;     // [fallback, seeding pass]
-  unsigned long long* fill_counts = ctl.p + 3;   // [tiny, small, large, huge]
-  unsigned int* fill_queue = reinterpret_cast<unsigned int*>(ctl.p + 7);
+  unsigned long long* fill_counts = ctl.p + 3;   // [tiny, small, medium, large, huge, huge chunks, most chunks]
+  unsigned int* fill_queue = reinterpret_cast<unsigned int*>(ctl.p + 10);
+  unsigned long long* task_ctr = ctl.p + 11;
   DBuf<uint32_t> need_full, shift, src, seed_seg, fb_list, p2_list;
   DBuf<uint64_t> read_cnt, read_off;
   GOD_TRY(need_full.alloc(n, st));
@@ -1000,15 +1099,16 @@ int seed_device(const god_index* idx, const uint8_t* d_reads, const uint64_t* d_
   sets.s[kSrcFB] = FB.view();
   sets.s[kSrcP2] = P2.view();
   GOD_TRY(exclusive_scan_u64(read_cnt.p, read_off.p, n, st));
-  DBuf<uint32_t> ltiny, lsmall, llarge, lhuge;
+  DBuf<uint32_t> ltiny, lsmall, lmedium, llarge, lhuge;
   GOD_TRY(ltiny.alloc(n, st));
   GOD_TRY(lsmall.alloc(n, st));
+  GOD_TRY(lmedium.alloc(n, st));
   GOD_TRY(llarge.alloc(n, st));
   GOD_TRY(lhuge.alloc(n, st));
-  GOD_LAUNCH(classify_reads, grid_for(n), kT, 0, st, n, read_off.p, ltiny.p, lsmall.p, llarge.p, lhuge.p,
-             fill_counts);
+  GOD_LAUNCH(classify_reads, grid_for(n), kT, 0, st, n, read_off.p, ltiny.p, lsmall.p, lmedium.p, llarge.p,
+             lhuge.p, fill_counts);
   uint64_t total = 0;
-  unsigned long long hf[4] = {0, 0, 0, 0};
+  unsigned long long hf[7] = {0, 0, 0, 0, 0, 0, 0};
   uint64_t set_tot[2] = {0, 0};
   GOD_CK(cudaMemcpyAsync(&total, read_off.p + n, 8, cudaMemcpyDeviceToHost, st));
   GOD_CK(cudaMemcpyAsync(hf, fill_counts, sizeof(hf), cudaMemcpyDeviceToHost, st));
@@ -1029,21 +1129,41 @@ int seed_device(const god_index* idx, const uint8_t* d_reads, const uint64_t* d_
   if (total == 0) return GOD_OK;
 
   // ---- fill + sort per read
-  const uint64_t n_tiny = hf[0], n_small = hf[1], n_large = hf[2], n_huge = hf[3];
+  const uint64_t n_tiny = hf[0], n_small = hf[1], n_medium = hf[2], n_large = hf[3], n_huge = hf[4];
   if (n_tiny)
     GOD_LAUNCH(fill_sort_tiny, grid_for(n_tiny, kT, 64), kT, 0, st, sets, src.p, seed_seg.p, read_off.p, ltiny.p,
                (uint32_t)n_tiny, idx->d_ent, out);
   if (n_small)
     GOD_LAUNCH(fill_sort_small, grid_for(n_small * 32, kT, 64), kT, 0, st, sets, src.p, seed_seg.p, read_off.p,
                lsmall.p, (uint32_t)n_small, idx->d_ent, out);
+  if (n_medium)
+    GOD_LAUNCH(fill_sort_medium, (unsigned)std::min<uint64_t>(n_medium, (uint64_t)num_sms() * 16), kMedThreads, 0,
+               st, sets, src.p, seed_seg.p, read_off.p, lmedium.p, (uint32_t)n_medium, idx->d_ent, out);
   if (n_large + n_huge) {
-    DBuf<uint64_t> tmp;
-    if (n_huge) GOD_TRY(tmp.alloc(2 * total, st));  // merge buffers, indexed by the read's anchor offset
+    // huge reads: one task per kLargeCap-anchor tile, two merge buffers per
+    // read in tmp (at twice its anchor offset), ceil(log2(most tiles)) levels
+    const uint64_t n_tasks = hf[5], most = hf[6];
+    if (n_tasks >= (1ull << 31)) {
+      set_error("seed: too many long anchor lists in one call");
+      return GOD_ERANGE;
+    }
+    DBuf<uint64_t> tmp, tasks;
+    if (n_huge) {
+      GOD_TRY(tmp.alloc(2 * total, st));
+      GOD_TRY(tasks.alloc(n_tasks, st));
+      GOD_LAUNCH(huge_tasks, grid_for(n_huge), kT, 0, st, lhuge.p, (uint32_t)n_huge, read_off.p, tasks.p, task_ctr);
+    }
     const size_t smem = 2 * kLargeCap * sizeof(uint64_t) + (kLargeThreads / 32) * 256 * 4 + 256 * 4;
     GOD_CK(cudaFuncSetAttribute(fill_sort_large, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const unsigned grid = (unsigned)std::min<uint64_t>(n_large + n_huge, (uint64_t)num_sms() * 3);
-    GOD_LAUNCH(fill_sort_large, grid, kLargeThreads, smem, st, sets, src.p, seed_seg.p, read_off.p, lhuge.p,
-               (uint32_t)n_huge, llarge.p, (uint32_t)n_large, idx->d_ent, out, tmp.p, fill_queue);
+    const unsigned grid = (unsigned)std::min<uint64_t>(n_large + n_tasks, (uint64_t)num_sms() * 3);
+    GOD_LAUNCH(fill_sort_large, grid, kLargeThreads, smem, st, sets, src.p, seed_seg.p, read_off.p, lhuge.p, tasks.p,
+               (uint32_t)n_tasks, llarge.p, (uint32_t)n_large, idx->d_ent, out, tmp.p, fill_queue);
+    int levels = 0;
+    while ((1ull << levels) < most) ++levels;
+    const unsigned mgrid = (unsigned)std::min<uint64_t>(std::max<uint64_t>(n_tasks, 1), (uint64_t)num_sms() * 8);
+    for (int L = 1; L <= levels; ++L)
+      GOD_LAUNCH(merge_huge_level, mgrid, kLargeThreads, 0, st, lhuge.p, tasks.p, (uint32_t)n_tasks, read_off.p, tmp.p,
+                 L, out);
   }
   return GOD_OK;
 }
