@@ -907,6 +907,7 @@ struct SetBufs {
   DBuf<uint32_t> seg_cnt;
   DBuf<uint64_t> seg_off;
   DBuf<uint32_t> max_m;      // longest segment (set by the segment builders)
+  uint32_t max_m_host = 0;   // its value, read back with the stream length
   uint64_t n_seg = 0;
   RecSet view() const { return RecSet{pz.p, sc.p, seg_off.p, seg_cnt.p}; }
 };
@@ -943,6 +944,7 @@ int sketch_and_lookup(const god_index* idx, const uint8_t* d_reads, SetBufs& B, 
   job.read_flag = read_flag;
   job.tune = idx->params.tune;
   job.max_m = max_m;
+  B.max_m_host = max_m;
   job.bytes_on_host = is_device_ptr(d_reads) ? 0 : 1;
   const DeviceIndex di = device_view(idx, via);
   const bool learned = via == 1 && di.leaves;
@@ -1054,10 +1056,17 @@ int seed_device(const god_index* idx, const uint8_t* d_reads, const uint64_t* d_
              seed_seg.p, read_cnt.p, fb_list.p, p2_list.p, pa_counts);
   unsigned long long hc[2] = {0, 0};
   uint64_t pa_tot = 0;
-  GOD_CK(cudaMemcpyAsync(hc, pa_counts, sizeof(hc), cudaMemcpyDeviceToHost, st));
-  GOD_CK(cudaMemcpyAsync(&pa_tot, PA.seg_off.p + PA.n_seg, 8, cudaMemcpyDeviceToHost, st));
-  GOD_CK(cudaStreamSynchronize(st));
-  GOD_TRY(scan_total_ok(pa_tot, "seed"));
+  // Both follow-up passes come from segments cut at the cap (a fallback for an
+  // N in a cut prefix, a seeding pass for a read whose chosen prefix was cut):
+  // when every segment is shorter than the cap there are none, and the counts
+  // need not be read back here (the record total is checked with the others).
+  const bool cut = PA.max_m_host >= cap;
+  if (cut) {
+    GOD_CK(cudaMemcpyAsync(hc, pa_counts, sizeof(hc), cudaMemcpyDeviceToHost, st));
+    GOD_CK(cudaMemcpyAsync(&pa_tot, PA.seg_off.p + PA.n_seg, 8, cudaMemcpyDeviceToHost, st));
+    GOD_CK(cudaStreamSynchronize(st));
+    GOD_TRY(scan_total_ok(pa_tot, "seed"));
+  }
   const uint64_t n_fb = hc[0], n_p2 = hc[1];
 
   // ---- fallback: full-length pattern alignment for reads with N in the prefix
@@ -1112,9 +1121,11 @@ int seed_device(const god_index* idx, const uint8_t* d_reads, const uint64_t* d_
   uint64_t set_tot[2] = {0, 0};
   GOD_CK(cudaMemcpyAsync(&total, read_off.p + n, 8, cudaMemcpyDeviceToHost, st));
   GOD_CK(cudaMemcpyAsync(hf, fill_counts, sizeof(hf), cudaMemcpyDeviceToHost, st));
+  if (!cut) GOD_CK(cudaMemcpyAsync(&pa_tot, PA.seg_off.p + PA.n_seg, 8, cudaMemcpyDeviceToHost, st));
   if (n_fb) GOD_CK(cudaMemcpyAsync(&set_tot[0], FB.seg_off.p + FB.n_seg, 8, cudaMemcpyDeviceToHost, st));
   if (n_p2) GOD_CK(cudaMemcpyAsync(&set_tot[1], P2.seg_off.p + P2.n_seg, 8, cudaMemcpyDeviceToHost, st));
   GOD_CK(cudaStreamSynchronize(st));
+  GOD_TRY(scan_total_ok(pa_tot, "seed"));
   GOD_TRY(scan_total_ok(total, "seed"));
   GOD_TRY(scan_total_ok(set_tot[0], "seed"));
   GOD_TRY(scan_total_ok(set_tot[1], "seed"));
