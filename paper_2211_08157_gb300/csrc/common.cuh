@@ -170,6 +170,9 @@ struct SketchJob {
                               // segments then run the one-thread-per-segment kernel
   int bytes_on_host;          // 1: `bytes` is page-locked host memory read over the host link
                               // (the per-segment kernel then stages each warp's span with wide loads)
+  const uint32_t* own;        // optional (per-segment kernel): segment g emits only the minimizers
+                              // whose k-mer index lies in [own[2g], own[2g + 1]) (the reference cut
+                              // into overlapping pieces, each owning the k-mers whose windows it holds)
 };
 
 // Runs the fused sparsify + 2-bit code + hash + window-minimum kernel over the

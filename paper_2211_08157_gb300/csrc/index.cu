@@ -44,6 +44,49 @@ __global__ void split_staged(const MinRec* __restrict__ staging, const uint32_t*
   }
 }
 
+// The same for the per-segment kernel's staging (segment s's records at
+// staging[base[s]]): a warp takes 32 consecutive segments and spreads their
+// records over its lanes; a lane finds the segment of its record by a binary
+// search over the segments' exclusive counts held one per lane.
+template <typename V>
+__global__ void split_staged_seg(const MinRec* __restrict__ staging, const uint32_t* __restrict__ cnt,
+                                 const uint64_t* __restrict__ off, uint64_t n_seg, const uint64_t* __restrict__ base,
+                                 uint64_t* __restrict__ keys, V* __restrict__ vals) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x / 32);
+  for (uint64_t grp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) / 32; grp * 32 < n_seg; grp += warps) {
+    const uint64_t sg = grp * 32 + lane;
+    const uint32_t c = sg < n_seg ? cnt[sg] : 0u;
+    const uint64_t b = sg < n_seg ? base[sg] : 0;
+    uint32_t inc = c;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t y = __shfl_up_sync(FULL, inc, d);
+      if (lane >= d) inc += y;
+    }
+    const uint32_t ex = inc - c;
+    const uint32_t tot = __shfl_sync(FULL, inc, 31);
+    const uint64_t o0 = off[grp * 32];
+    for (uint32_t b0 = 0; b0 < tot; b0 += 32) {   // warp-uniform trip count
+      const uint32_t i = b0 + lane;
+      int L = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        const uint32_t e = __shfl_sync(FULL, ex, L + step);
+        if (e <= i) L += step;
+      }
+      const uint32_t eL = __shfl_sync(FULL, ex, L);
+      const uint64_t bL = __shfl_sync(FULL, b, L);
+      if (i < tot) {
+        const uint4 r = __ldcs(reinterpret_cast<const uint4*>(staging + bL + (i - eL)));   // read once
+        keys[o0 + i] = ((uint64_t)r.y << 32) | r.x;
+        vals[o0 + i] = (V)(((uint64_t)r.z << 1) | (r.w & 1u));
+      }
+    }
+  }
+}
+
 // Runs of equal keys in the sorted array: the first element of each run
 // (its head) finds the run's end by galloping then bisecting, and records
 // rv[i] = 1 << 32 | length for a kept run (length <= max_occ), 0 otherwise.
@@ -176,7 +219,12 @@ int sort_and_emit(god_index* idx, StagedSketch& S, uint64_t n, cudaStream_t st, 
   GOD_TRY(keys.alloc(n, st));
   GOD_TRY(vals.alloc(n, st));
   const unsigned g = std::min<unsigned>(blocks_for(n), (unsigned)num_sms() * 32);
-  if (n) {
+  if (n && S.sub_base) {
+    const uint64_t blocks =
+        std::min<uint64_t>(((S.n_sub + 31) / 32 * 32 + kThreads - 1) / kThreads, (uint64_t)num_sms() * 16);
+    GOD_LAUNCH(split_staged_seg<V>, (unsigned)blocks, kThreads, 0, st, S.staging.p, S.sub_cnt.p, S.sub_off.p,
+               S.n_sub, S.sub_base, keys.p, vals.p);
+  } else if (n) {
     const uint64_t blocks = std::min<uint64_t>((S.n_sub * 32 + kThreads - 1) / kThreads, (uint64_t)num_sms() * 16);
     GOD_LAUNCH(split_staged<V>, (unsigned)blocks, kThreads, 0, st, S.staging.p, S.sub_cnt.p, S.sub_off.p, S.n_sub,
                S.WT, keys.p, vals.p);
@@ -212,32 +260,119 @@ int sort_and_emit(god_index* idx, StagedSketch& S, uint64_t n, cudaStream_t st, 
 }
 
 // ------------------------------------------------------------------ build
+// The reference cut into overlapping pieces for the one-thread-per-segment
+// sketch kernel: piece i owns the k-mers [i S, (i + 1) S) of the patterned
+// reference and holds every window containing one of them (w - 1 k-mers
+// before, w - 1 after, and the k - 1 bases of the last k-mer), starting at a
+// multiple of the pattern weight x so that its first base has pattern phase 0.
+// Its minimizers in the owned range are exactly the whole sequence's there.
+// Piece i spans [a_i, b_i) with a_0 = 0, a_i = i S - cw (cw = w - 1 rounded
+// up to a multiple of x) and b_i = min(m, (i + 1) S + c) (c = w + k - 2), so
+// the virtual offsets (sums of b - a + 1) have a closed form and the pieces
+// are generated on the device (no host loop, no descriptor copy).
+struct RefPieces {
+  uint64_t n = 0, S = 0, cw = 0, c = 0, m = 0, nk = 0, T = 0;
+  uint32_t x = 1, p = 1, max_m = 0;
+};
+
+__host__ __device__ inline uint64_t ref_voff(const RefPieces& R, uint64_t i) {
+  const uint64_t t = i < R.T ? i : R.T;   // pieces before i that end inside the reference
+  const uint64_t sb = R.S * t * (t + 1) / 2 + R.c * t + (i - t) * R.m;
+  const uint64_t sa = i ? R.S * i * (i - 1) / 2 - R.cw * (i - 1) : 0;
+  return sb - sa + i;
+}
+
+__global__ void make_ref_pieces(RefPieces R, SegDesc* __restrict__ segs, uint64_t* __restrict__ voff,
+                                uint32_t* __restrict__ own) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i <= R.n; i += (uint64_t)gridDim.x * blockDim.x) {
+    voff[i] = ref_voff(R, i);
+    if (i == R.n) continue;
+    const uint64_t lo = i * R.S, hi = lo + R.S < R.nk ? lo + R.S : R.nk;
+    const uint64_t a = i ? lo - R.cw : 0;
+    const uint64_t b = lo + R.S + R.c < R.m ? lo + R.S + R.c : R.m;
+    segs[i] = SegDesc{0, (uint32_t)(b - a), 0, (uint32_t)((uint64_t)R.p * (a / R.x)), 0};
+    own[2 * i] = (uint32_t)(lo - a);
+    own[2 * i + 1] = (uint32_t)(hi - a);
+  }
+}
+
+bool ref_pieces(const PatternInfo& P, uint64_t m, int k, int w, RefPieces* R) {
+  const uint64_t x = (uint64_t)P.x;
+  const uint64_t cw = ((uint64_t)(w - 1) + x - 1) / x * x, c = (uint64_t)(w + k - 2);
+  if (m < (uint64_t)k) return false;
+  // piece length (patterned bases): short enough for every SM to hold its
+  // warps two rounds over (a warp takes 32 pieces; about 24 warps per SM),
+  // at least 256 (the halo's share of the work), at most 2048
+  const uint64_t lanes = (uint64_t)num_sms() * 24 * 32 * 2;
+  const uint64_t span = std::min<uint64_t>(2048, std::max<uint64_t>(256, m / lanes + cw + c));
+  if (span <= cw + c + x) return false;
+  R->S = (span - cw - c) / x * x;
+  R->cw = cw;
+  R->c = c;
+  R->m = m;
+  R->nk = m - k + 1;
+  R->n = (R->nk + R->S - 1) / R->S;
+  R->T = m >= c ? (m - c) / R->S : 0;
+  R->x = (uint32_t)x;
+  R->p = (uint32_t)P.p;
+  R->max_m = (uint32_t)(R->S + cw + c);
+  return R->n >= 1024 && R->n < (1ull << 31);   // long references only
+}
+
 int build_index_device(god_index* idx, const uint8_t* d_ref, uint64_t len, cudaStream_t st) {
   const PatternInfo& P = idx->pat;
   const uint64_t m = patterned_len(P, len, 0);
   idx->n_min = idx->n_keys = idx->n_ent = 0;
   DBuf<SegDesc> seg;
   DBuf<uint64_t> voff;
-  GOD_TRY(seg.alloc(1, st));
-  GOD_TRY(voff.alloc(2, st));
-  SegDesc hs{0, (uint32_t)m, 0, 0, 0};
-  uint64_t hv[2] = {0, m + 1};
-  GOD_CK(cudaMemcpyAsync(seg.p, &hs, sizeof(hs), cudaMemcpyHostToDevice, st));
-  GOD_CK(cudaMemcpyAsync(voff.p, hv, sizeof(hv), cudaMemcpyHostToDevice, st));
-
+  DBuf<uint32_t> own;
   SketchJob job{};
   job.bytes = d_ref;
-  job.segs = seg.p;
-  job.seg_voff = voff.p;
-  job.n_seg = 1;
-  job.V = m + 1;
   job.k = idx->k;
   job.w = idx->w;
   job.pat = P;
   job.tune = idx->params.tune;
+  RefPieces R;
   StagedSketch S;
-  GOD_TRY(run_sketch_staged(job, st, S, nullptr));
-  const uint64_t n = S.total;
+  uint64_t n = 0;
+  bool pieces = ref_pieces(P, m, idx->k, idx->w, &R);
+  if (pieces) {
+    job.n_seg = (uint32_t)R.n;
+    job.V = ref_voff(R, R.n);
+    job.max_m = R.max_m;
+    pieces = sketch_segments_ok(job);
+  }
+  if (pieces) {
+    const uint64_t np = R.n;
+    GOD_TRY(seg.alloc(np, st));
+    GOD_TRY(voff.alloc(np + 1, st));
+    GOD_TRY(own.alloc(2 * np, st));
+    GOD_LAUNCH(make_ref_pieces, (unsigned)std::min<uint64_t>((np + kThreads) / kThreads, (uint64_t)num_sms() * 8),
+               kThreads, 0, st, R, seg.p, voff.p, own.p);
+    job.segs = seg.p;
+    job.seg_voff = voff.p;
+    job.own = own.p;
+    GOD_TRY(run_sketch_segments(job, st, S));
+    GOD_CK(cudaMemcpyAsync(&n, S.sub_off.p + S.n_sub, 8, cudaMemcpyDeviceToHost, st));
+    GOD_CK(cudaStreamSynchronize(st));
+    GOD_TRY(scan_total_ok(n, "index"));
+    S.total = n;
+  } else {
+    GOD_TRY(seg.alloc(1, st));
+    GOD_TRY(voff.alloc(2, st));
+    SegDesc hs{0, (uint32_t)m, 0, 0, 0};
+    uint64_t hv[2] = {0, m + 1};
+    GOD_CK(cudaMemcpyAsync(seg.p, &hs, sizeof(hs), cudaMemcpyHostToDevice, st));
+    GOD_CK(cudaMemcpyAsync(voff.p, hv, sizeof(hv), cudaMemcpyHostToDevice, st));
+    job.segs = seg.p;
+    job.seg_voff = voff.p;
+    job.n_seg = 1;
+    job.V = m + 1;
+    job.own = nullptr;
+    job.max_m = 0;
+    GOD_TRY(run_sketch_staged(job, st, S, nullptr));
+    n = S.total;
+  }
   idx->n_min = n;
 
   DBuf<uint64_t> okeys, oent;

@@ -3,7 +3,10 @@
 // short: short reads at every shift, the capped pattern-alignment prefixes of
 // long reads).
 //
-// A warp takes 32 consecutive segments, one per lane. When the bytes are in
+// A warp takes 32 consecutive segments, one per lane. The reference is cut
+// into overlapping pieces for this kernel: each piece owns a range of k-mers
+// and holds every window that contains one of them, so its minimizers in that
+// range are the whole sequence's. When the bytes are in
 // page-locked host memory (read over the host link), the warp first loads
 // their span (for short reads one contiguous stretch) as aligned 16-byte
 // words, coded in 2 bits on the way, into shared memory; device-resident
@@ -151,6 +154,12 @@ __global__ void __launch_bounds__(kSegThreads, (W <= 11 ? 6 : 3)) sketch_seg_ker
     KT pm = 0, px = 0;
     uint32_t zr = 0;                            // strand bits of the last 32 k-mers (bit 0 = newest)
     MinRec* out = a.staging + (g < J.n_seg ? J.seg_voff[g] : 0);
+    uint32_t olo = 0, ohi = 0xFFFFFFFFu;        // owned k-mer indices
+    if (J.own && g < J.n_seg) {
+      const uint2 ow = reinterpret_cast<const uint2*>(J.own)[g];
+      olo = ow.x;
+      ohi = ow.y;
+    }
     const uint32_t steps = nk ? nk + W - 1 : 0;
     for (uint32_t j0 = 0; j0 < steps; j0 += W) {
 #pragma unroll
@@ -188,8 +197,8 @@ __global__ void __launch_bounds__(kSegThreads, (W <= 11 ? 6 : 3)) sketch_seg_ker
         const KT Y = t == W - 1 ? px : max(D[t + 1], px);
         if (j >= (uint32_t)W - 1) {
           const KT ku = B[t + 1 < W ? t + 1 : 0];   // key of k-mer u = j - W + 1
-          if (ku == Y && ku != 0 && ku != PALIN) {
-            const uint32_t u = j - (W - 1);
+          const uint32_t u = j - (W - 1);
+          if (ku == Y && ku != 0 && ku != PALIN && u >= olo && u < ohi) {
             uint32_t q = u, rr = 0;
             if (!X1) divmod_x(u, (uint32_t)x, xinv, q, rr);
             MinRec rec;

@@ -49,9 +49,14 @@ def test_autotuned_launch_same_anchors(env):
     ka, _, _ = god.god_index_export(base)
     kb, _, _ = god.god_index_export(tuned)
     assert np.array_equal(ka, kb)
-    # the reference's pass runs the tile kernel with a tuned shape; the reads'
-    # short segments run the one-thread-per-segment kernel, which has no shape
-    # to choose
+    # short segments (the reads above, the reference's pieces) run the
+    # one-thread-per-segment kernel, which has no shape to choose; long reads'
+    # full-length segments run the tile kernel with a tuned shape
+    lreads, loffs, _ = synth.reads(ref, 300, synth.HIFI, synth.HIFI_ERR, 62)
+    la = _seed(god, base, lreads, loffs)
+    lb = _seed(god, tuned, lreads, loffs)
+    lwant, _ = oracle.Index(ref, "10", 21, 11, 500).seed(lreads, loffs, 32)
+    assert np.array_equal(la, lb) and np.array_equal(la.reshape(-1), lwant.view(np.uint32))
     table = god.god_autotune_report()
     assert len(table) >= 1 and all(e["threads"] in (128, 256) and e["chunks"] in (1, 2) for e in table)
 
