@@ -368,6 +368,12 @@ uint64_t god_launch_count(void);
 void god_prof_enable(int on);
 void god_prof_reset(void);
 int god_prof_report(char *buf, uint64_t cap);
+/* The timed launches since the last reset as a JSON list of [kernel, stream,
+ * start_ms, end_ms] (streams numbered in order of appearance; times from an
+ * event recorded on the default stream when timing was switched on or reset),
+ * for seeing how launches on several streams overlap. Same return convention
+ * as god_prof_report; at most 2^20 launches are kept. */
+int god_prof_timeline(char *buf, uint64_t cap);
 
 /* The batched sketch pass is captured into a CUDA graph per (shape, stream)
  * and replayed (on by default; calls on the legacy default stream launch

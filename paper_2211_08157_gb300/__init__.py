@@ -339,6 +339,18 @@ def god_prof_report() -> dict:
     return {k: (int(v[0]), float(v[1]), float(v[2]), float(v[3])) for k, v in json.loads(buf.value.decode()).items()}
 
 
+def god_prof_timeline() -> list:
+    """Timed launches as [(kernel, stream number, start ms, end ms)]."""
+    import json
+    L = load()
+    need = L.god_prof_timeline(None, 0)
+    buf = C.create_string_buffer(max(need, 2) + 64)
+    rc = L.god_prof_timeline(buf, len(buf))
+    if rc != 0:
+        raise RuntimeError("profile timeline buffer too small")
+    return [(k, int(s), float(a), float(b)) for k, s, a, b in json.loads(buf.value.decode())]
+
+
 # ---------------------------------------------------------------- serving
 class GodServer:
     def __init__(self, index: GodIndex, slots: int = 4, mem_budget: int = 0, max_batch_bases: int = 0):

@@ -146,6 +146,7 @@ SIGNATURES = {
     "god_launch_count": (U64, []),
     "god_prof_enable": (None, [I32]),
     "god_prof_reset": (None, []),
+    "god_prof_timeline": (I32, [C.c_char_p, U64]),
     "god_prof_report": (I32, [C.c_char_p, U64]),
     "god_set_graphs": (None, [I32]),
     "god_autotune_report": (I32, [C.c_char_p, U64]),

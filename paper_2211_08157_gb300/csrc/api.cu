@@ -24,7 +24,16 @@ static thread_local std::string t_last_error;
 struct ProfPending {
   const char* name;
   cudaEvent_t a, b;
+  cudaStream_t st;
 };
+// Optional timeline: every timed launch as (kernel, stream, start, end) in ms
+// after the base event recorded when timing was switched on or reset.
+struct ProfSpan {
+  const char* name;
+  uintptr_t st;
+  float t0, t1;
+};
+constexpr size_t kProfSpanCap = 1u << 20;
 struct ProfTotal {
   uint64_t launches = 0;
   double ms = 0.0;
@@ -35,6 +44,8 @@ static std::mutex g_prof_mu;
 static std::vector<ProfPending> g_prof_pending;
 static std::vector<cudaEvent_t> g_prof_free;
 static std::map<std::string, ProfTotal> g_prof_tot;
+static std::vector<ProfSpan> g_prof_spans;
+static cudaEvent_t g_prof_base = nullptr;
 
 static cudaEvent_t prof_event() {
   cudaEvent_t e = nullptr;
@@ -69,7 +80,7 @@ void prof_end(const char* name, cudaStream_t st, cudaEvent_t a) {
   cudaEvent_t b = prof_event();
   prof_record(b, st);
   std::lock_guard<std::mutex> lk(g_prof_mu);
-  g_prof_pending.push_back(ProfPending{name, a, b});
+  g_prof_pending.push_back(ProfPending{name, a, b, st});
 }
 
 void prof_add_work(const char* name, double bytes, double units) {
@@ -135,10 +146,14 @@ static void prof_collect() {
     g_prof_slots.push_back(c.slot);
   }
   for (auto& p : pend) {
-    float ms = 0.0f;
+    float ms = 0.0f, t0 = 0.0f;
     cudaEventSynchronize(p.b);
     cudaEventElapsedTime(&ms, p.a, p.b);
+    const bool span = g_prof_base && cudaEventElapsedTime(&t0, g_prof_base, p.a) == cudaSuccess;
+    if (!span) cudaGetLastError();
     std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (span && g_prof_spans.size() < kProfSpanCap)
+      g_prof_spans.push_back(ProfSpan{p.name, reinterpret_cast<uintptr_t>(p.st), t0, t0 + ms});
     ProfTotal& t = g_prof_tot[p.name];
     t.launches++;
     t.ms += ms;
@@ -376,8 +391,18 @@ uint64_t god_launch_count(void) { return g_launches.load(); }
 
 void god_set_graphs(int on) { g_graphs_on.store(on ? 1 : 0); }
 
+static void prof_mark_base() {
+  if (!g_prof_base && cudaEventCreate(&g_prof_base) != cudaSuccess) {
+    cudaGetLastError();
+    g_prof_base = nullptr;
+    return;
+  }
+  cudaEventRecord(g_prof_base, 0);
+}
+
 void god_prof_enable(int on) {
   if (!on) prof_collect();
+  else if (!g_prof_base) prof_mark_base();
   g_prof_on.store(on == 2 ? 2 : (on ? 1 : 0));
 }
 
@@ -385,6 +410,29 @@ void god_prof_reset(void) {
   prof_collect();
   std::lock_guard<std::mutex> lk(g_prof_mu);
   g_prof_tot.clear();
+  g_prof_spans.clear();
+  prof_mark_base();
+}
+
+int god_prof_timeline(char* buf, uint64_t cap) {
+  prof_collect();
+  std::string out = "[";
+  {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    std::map<uintptr_t, int> ids;
+    for (size_t i = 0; i < g_prof_spans.size(); ++i) {
+      const ProfSpan& sp = g_prof_spans[i];
+      auto it = ids.find(sp.st);
+      const int id = it == ids.end() ? (ids[sp.st] = (int)ids.size()) : it->second;
+      char item[256];
+      snprintf(item, sizeof item, "%s[\"%s\", %d, %.4f, %.4f]", i ? ", " : "", sp.name, id, sp.t0, sp.t1);
+      out += item;
+    }
+  }
+  out += "]";
+  if (!buf || cap < out.size() + 1) return (int)(out.size() + 1);
+  memcpy(buf, out.c_str(), out.size() + 1);
+  return 0;
 }
 
 int god_prof_report(char* buf, uint64_t cap) {
