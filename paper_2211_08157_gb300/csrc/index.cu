@@ -335,9 +335,11 @@ int build_index_device(god_index* idx, const uint8_t* d_ref, uint64_t len, cudaS
   RefPieces R;
   StagedSketch S;
   uint64_t n = 0;
-  bool pieces = ref_pieces(P, m, idx->k, idx->w, &R);
+  // pieces only for a device-resident reference: 32 pieces span more bytes
+  // than a warp stages, and the tile kernel's coalesced gather reads
+  // page-locked host bytes better than one lane per piece
+  bool pieces = is_device_ptr(d_ref) && ref_pieces(P, m, idx->k, idx->w, &R);
   if (pieces) {
-    job.bytes_on_host = is_device_ptr(d_ref) ? 0 : 1;   // page-locked host bytes: staged per warp
     job.n_seg = (uint32_t)R.n;
     job.V = ref_voff(R, R.n);
     job.max_m = R.max_m;
