@@ -48,7 +48,7 @@ struct SegArgs {
   uint32_t* sub_cnt;
 };
 
-template <typename KT, int HM, int W, bool STAGE, bool X1>
+template <typename KT, int HM, int W, bool STAGE, bool X1, int KC>
 __global__ void __launch_bounds__(kSegThreads, (W <= 11 ? 6 : 3)) sketch_seg_kernel(const __grid_constant__ SegArgs a) {
   extern __shared__ __align__(16) unsigned char seg_smem[];
   constexpr int ROW = 2 * W + 1;              // keys B[W], minima C[W]; odd stride: no bank conflicts
@@ -57,7 +57,9 @@ __global__ void __launch_bounds__(kSegThreads, (W <= 11 ? 6 : 3)) sketch_seg_ker
   __shared__ uint8_t s_lut[256];
   __shared__ uint32_t s_off[kMaxPattern], s_delta[kMaxPattern];
   const SketchJob& J = a.job;
-  const int p = J.pat.p, x = J.pat.x, k = J.k;
+  // KC > 0: k fixed at compile time (the preset shapes), so the masks, shifts
+  // and the palindrome test fold into constants
+  const int p = J.pat.p, x = KC && X1 ? 1 : J.pat.x, k = KC ? KC : J.k;
   for (int i = threadIdx.x; i < 256; i += blockDim.x) s_lut[i] = (uint8_t)base_code((uint8_t)i);
   for (int i = threadIdx.x; i < x; i += blockDim.x) {
     s_off[i] = (uint32_t)J.pat.off[i];
@@ -227,14 +229,11 @@ __global__ void __launch_bounds__(kSegThreads, (W <= 11 ? 6 : 3)) sketch_seg_ker
   }
 }
 
-template <typename KT, int HM, int W>
-int launch_seg(const SegArgs& a, cudaStream_t st) {
-  const bool x1 = a.job.pat.x == 1;
-  auto sketch_seg = a.job.bytes_on_host
-                        ? (x1 ? sketch_seg_kernel<KT, HM, W, true, true> : sketch_seg_kernel<KT, HM, W, true, false>)
-                        : (x1 ? sketch_seg_kernel<KT, HM, W, false, true> : sketch_seg_kernel<KT, HM, W, false, false>);
+template <typename KT, int HM, int W, bool STAGE, bool X1, int KC>
+int launch_variant(const SegArgs& a, cudaStream_t st) {
+  auto sketch_seg = sketch_seg_kernel<KT, HM, W, STAGE, X1, KC>;
   const size_t rows = ((size_t)kSegThreads * (2 * W + 1) * sizeof(KT) + 15) & ~(size_t)15;
-  const size_t smem = rows + (a.job.bytes_on_host ? (size_t)(kSegThreads / 32) * kWarpBytes : 0);
+  const size_t smem = rows + (STAGE ? (size_t)(kSegThreads / 32) * kWarpBytes : 0);
   GOD_CK(cudaFuncSetAttribute(sketch_seg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   GOD_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sketch_seg, kSegThreads, smem));
@@ -245,9 +244,35 @@ int launch_seg(const SegArgs& a, cudaStream_t st) {
   return GOD_OK;
 }
 
+// Any k: the pattern weight and the staging choose the variant.
+template <typename KT, int HM, int W>
+int launch_seg(const SegArgs& a, cudaStream_t st) {
+  const bool x1 = a.job.pat.x == 1;
+  if (a.job.bytes_on_host)
+    return x1 ? launch_variant<KT, HM, W, true, true, 0>(a, st) : launch_variant<KT, HM, W, true, false, 0>(a, st);
+  return x1 ? launch_variant<KT, HM, W, false, true, 0>(a, st) : launch_variant<KT, HM, W, false, false, 0>(a, st);
+}
+
+// A preset shape with k (and the pattern weight's case) fixed at compile time.
+template <typename KT, int HM, int W, int KC, bool X1>
+int launch_seg_k(const SegArgs& a, cudaStream_t st) {
+  if (a.job.bytes_on_host) return launch_variant<KT, HM, W, true, X1, KC>(a, st);
+  return launch_variant<KT, HM, W, false, X1, KC>(a, st);
+}
+
 template <int W>
 int launch_seg_w(const SegArgs& a, cudaStream_t st) {
   const int k = a.job.k;
+  const bool x1 = a.job.pat.x == 1;
+  // the preset shapes: k21 w11 and k15 w10 with weight-1 patterns, k19 w19
+  // with heavier ones
+  if constexpr (W == 11) {
+    if (k == 21 && x1) return launch_seg_k<uint64_t, 1, W, 21, true>(a, st);
+  } else if constexpr (W == 10) {
+    if (k == 15 && x1) return launch_seg_k<uint32_t, 0, W, 15, true>(a, st);
+  } else if constexpr (W == 19) {
+    if (k == 19 && !x1) return launch_seg_k<uint64_t, 1, W, 19, false>(a, st);
+  }
   if (2 * k <= 30) return launch_seg<uint32_t, 0, W>(a, st);
   if (2 * k <= 32) return launch_seg<uint64_t, 0, W>(a, st);
   if (2 * k <= 46) return launch_seg<uint64_t, 1, W>(a, st);
