@@ -200,7 +200,8 @@ __global__ void __launch_bounds__(kSegThreads, (W <= 11 ? 6 : 3)) sketch_seg_ker
         if (j >= (uint32_t)W - 1) {
           const KT ku = B[t + 1 < W ? t + 1 : 0];   // key of k-mer u = j - W + 1
           const uint32_t u = j - (W - 1);
-          if (ku == Y && ku != 0 && ku != PALIN && u >= olo && u < ohi) {
+          // (odd k: a k-mer is never its own reverse complement)
+          if (ku == Y && ku != 0 && ((KC & 1) || ku != PALIN) && u >= olo && u < ohi) {
             uint32_t q = u, rr = 0;
             if (!X1) divmod_x(u, (uint32_t)x, xinv, q, rr);
             MinRec rec;
