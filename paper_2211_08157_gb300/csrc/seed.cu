@@ -32,6 +32,7 @@ constexpr int kT = 256;
 constexpr uint32_t kSrcPA = 0, kSrcFB = 1, kSrcP2 = 2;
 constexpr int kSmallCap = 128;          // anchors per read for the warp path
 constexpr int kMedThreads = 128;
+constexpr int kWarpCap = 512;           // anchors per read for the warp bitonic path
 constexpr int kMedCap = 1024;           // anchors per read for the medium CTA path
 constexpr int kLargeThreads = 256;
 constexpr int kLargeCap = 4096;         // anchors sorted in shared memory at once
@@ -219,23 +220,24 @@ __global__ void count_anchors_list(const uint32_t* __restrict__ list, uint32_t n
 
 // Reads by anchor-list length: tiny (thread path), small (warp path), large
 // (CTA path). Lists are unordered; every read writes its own output range.
-// counts: [tiny, small, medium, large, huge reads, chunks of the huge reads
-// (kLargeCap anchors each), most chunks of one read].
+// counts: [tiny, small, warp, medium, large, huge reads, chunks of the huge
+// reads (kLargeCap anchors each), most chunks of one read].
 __global__ void classify_reads(uint32_t n, const uint64_t* __restrict__ read_off, uint32_t* __restrict__ tiny,
-                               uint32_t* __restrict__ small, uint32_t* __restrict__ medium,
-                               uint32_t* __restrict__ large, uint32_t* __restrict__ huge,
-                               unsigned long long* __restrict__ counts) {
+                               uint32_t* __restrict__ small, uint32_t* __restrict__ warpl,
+                               uint32_t* __restrict__ medium, uint32_t* __restrict__ large,
+                               uint32_t* __restrict__ huge, unsigned long long* __restrict__ counts) {
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t c = read_off[i + 1] - read_off[i];
     warp_append(c > 0 && c <= kTinyCap, (uint32_t)i, tiny, counts + 0);
     warp_append(c > kTinyCap && c <= kSmallCap, (uint32_t)i, small, counts + 1);
-    warp_append(c > kSmallCap && c <= kMedCap, (uint32_t)i, medium, counts + 2);
-    warp_append(c > kMedCap && c <= kLargeCap, (uint32_t)i, large, counts + 3);
-    warp_append(c > kLargeCap, (uint32_t)i, huge, counts + 4);
+    warp_append(c > kSmallCap && c <= kWarpCap, (uint32_t)i, warpl, counts + 2);
+    warp_append(c > kWarpCap && c <= kMedCap, (uint32_t)i, medium, counts + 3);
+    warp_append(c > kMedCap && c <= kLargeCap, (uint32_t)i, large, counts + 4);
+    warp_append(c > kLargeCap, (uint32_t)i, huge, counts + 5);
     if (c > kLargeCap) {
       const unsigned long long ch = (c + kLargeCap - 1) / kLargeCap;
-      atomicAdd(counts + 5, ch);
-      atomicMax(counts + 6, ch);
+      atomicAdd(counts + 6, ch);
+      atomicMax(counts + 7, ch);
     }
   }
 }
@@ -479,7 +481,86 @@ __device__ void bitonic_sort_smem(uint64_t* s, uint32_t n_pad) {
   }
 }
 
-// Medium anchor lists (kSmallCap < n <= kMedCap; short reads on repeat-rich
+// Anchor lists of kSmallCap < n <= kWarpCap (short reads on repeat-rich
+// references): one warp per read, 4 KB of keys in shared memory, the
+// records' entries expanded by the whole warp (a lane finds the record of
+// entry q by a binary search over the lanes' exclusive counts), and a
+// bitonic network over the padded list with warp barriers only (no CTA-wide
+// barrier per stage, so the warps of an SM interleave freely).
+__global__ void __launch_bounds__(kT) fill_sort_warp(RecSets sets, const uint32_t* __restrict__ src,
+                                                     const uint32_t* __restrict__ seed_seg,
+                                                     const uint64_t* __restrict__ read_off,
+                                                     const uint32_t* __restrict__ list, uint32_t nl,
+                                                     const uint64_t* __restrict__ ent, god_anchor* __restrict__ out) {
+  __shared__ uint64_t buf[kT / 32][kWarpCap];
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint64_t* B = buf[wid];
+  const uint64_t warps = (uint64_t)gridDim.x * (kT / 32);
+  for (uint64_t li = (blockIdx.x * (uint64_t)kT + threadIdx.x) / 32; li < nl; li += warps) {
+    const uint32_t i = list[li];
+    const uint64_t off = read_off[i];
+    const uint32_t n = (uint32_t)(read_off[i + 1] - off);
+    const RecSet S = pick_set(sets, src[i]);
+    const uint32_t g = seed_seg[i];
+    const uint64_t beg = S.seg_off[g];
+    const uint32_t cnt = S.seg_cnt[g];
+    uint32_t base = 0;
+    for (uint32_t r0 = 0; r0 < cnt; r0 += 32) {
+      const uint32_t r = r0 + lane;
+      uint32_t c = 0, start = 0, pzv = 0;
+      if (r < cnt) {
+        const uint64_t sc = S.sc[beg + r];
+        c = (uint32_t)(sc >> 32);
+        start = (uint32_t)sc;
+        if (c) pzv = S.pz[beg + r];
+      }
+      uint32_t incl = c;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, incl, d);
+        if (lane >= d) incl += y;
+      }
+      const uint32_t ex = incl - c;
+      const uint32_t tot = __shfl_sync(FULL, incl, 31);
+      for (uint32_t q0 = 0; q0 < tot; q0 += 32) {   // warp-uniform trip count
+        const uint32_t q = q0 + lane;
+        int L = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+          const uint32_t e = __shfl_sync(FULL, ex, L + step);
+          if (e <= q) L += step;
+        }
+        const uint32_t eL = __shfl_sync(FULL, ex, L);
+        const uint32_t sL = __shfl_sync(FULL, start, L);
+        const uint32_t pL = __shfl_sync(FULL, pzv, L);
+        if (q < tot) B[base + q] = anchor_key(__ldg(ent + sL + (q - eL)), pL >> 1, pL & 1u);
+      }
+      base += tot;
+    }
+    uint32_t n_pad = 32;
+    while (n_pad < n) n_pad <<= 1;
+    for (uint32_t q = n + lane; q < n_pad; q += 32) B[q] = ~0ULL;
+    __syncwarp();
+    for (uint32_t kk = 2; kk <= n_pad; kk <<= 1) {
+      for (uint32_t jj = kk >> 1; jj > 0; jj >>= 1) {
+        for (uint32_t t = lane; t < n_pad / 2; t += 32) {
+          const uint32_t lo = ((t & ~(jj - 1)) << 1) | (t & (jj - 1)), hi = lo + jj;
+          const uint64_t a = B[lo], b = B[hi];
+          if ((a > b) == ((lo & kk) == 0)) {
+            B[lo] = b;
+            B[hi] = a;
+          }
+        }
+        __syncwarp();
+      }
+    }
+    for (uint32_t q = lane; q < n; q += 32) store_anchor(out + off + q, i, B[q]);
+    __syncwarp();
+  }
+}
+
+// Medium anchor lists (kWarpCap < n <= kMedCap; short reads on repeat-rich
 // references): a 128-thread CTA per read, the keys in 8 KB of shared memory
 // (16 CTAs fit an SM, where the 256-thread large path with its 74 KB fit 3 and
 // spent its time waiting at barriers), entries expanded by all threads (a
@@ -1022,15 +1103,16 @@ int seed_device(const god_index* idx, const uint8_t* d_reads, const uint64_t* d_
   }
 
   // small per-call state: error flag, list counters and work queues in one buffer
-  constexpr int kCtl = 12;
+  constexpr int kCtl = 13;
   DBuf<unsigned long long> ctl;
   GOD_TRY(ctl.alloc(kCtl, st));
   GOD_CK(cudaMemsetAsync(ctl.p, 0, kCtl * sizeof(unsigned long long), st));
   int* err = reinterpret_cast<int*>(ctl.p);
   unsigned long long* pa_counts = ctl.p + 1;     // [fallback, seeding pass]
-  unsigned long long* fill_counts = ctl.p + 3;   // [tiny, small, medium, large, huge, huge chunks, most chunks]
-  unsigned int* fill_queue = reinterpret_cast<unsigned int*>(ctl.p + 10);
-  unsigned long long* task_ctr = ctl.p + 11;
+  // [tiny, small, warp, medium, large, huge, huge chunks, most chunks]
+  unsigned long long* fill_counts = ctl.p + 3;
+  unsigned int* fill_queue = reinterpret_cast<unsigned int*>(ctl.p + 11);
+  unsigned long long* task_ctr = ctl.p + 12;
   DBuf<uint32_t> need_full, shift, src, seed_seg, fb_list, p2_list;
   DBuf<uint64_t> read_cnt, read_off;
   GOD_TRY(need_full.alloc(n, st));
@@ -1108,16 +1190,17 @@ int seed_device(const god_index* idx, const uint8_t* d_reads, const uint64_t* d_
   sets.s[kSrcFB] = FB.view();
   sets.s[kSrcP2] = P2.view();
   GOD_TRY(exclusive_scan_u64(read_cnt.p, read_off.p, n, st));
-  DBuf<uint32_t> ltiny, lsmall, lmedium, llarge, lhuge;
+  DBuf<uint32_t> ltiny, lsmall, lwarp, lmedium, llarge, lhuge;
   GOD_TRY(ltiny.alloc(n, st));
   GOD_TRY(lsmall.alloc(n, st));
+  GOD_TRY(lwarp.alloc(n, st));
   GOD_TRY(lmedium.alloc(n, st));
   GOD_TRY(llarge.alloc(n, st));
   GOD_TRY(lhuge.alloc(n, st));
-  GOD_LAUNCH(classify_reads, grid_for(n), kT, 0, st, n, read_off.p, ltiny.p, lsmall.p, lmedium.p, llarge.p,
-             lhuge.p, fill_counts);
+  GOD_LAUNCH(classify_reads, grid_for(n), kT, 0, st, n, read_off.p, ltiny.p, lsmall.p, lwarp.p, lmedium.p,
+             llarge.p, lhuge.p, fill_counts);
   uint64_t total = 0;
-  unsigned long long hf[7] = {0, 0, 0, 0, 0, 0, 0};
+  unsigned long long hf[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   uint64_t set_tot[2] = {0, 0};
   GOD_CK(cudaMemcpyAsync(&total, read_off.p + n, 8, cudaMemcpyDeviceToHost, st));
   GOD_CK(cudaMemcpyAsync(hf, fill_counts, sizeof(hf), cudaMemcpyDeviceToHost, st));
@@ -1140,20 +1223,24 @@ int seed_device(const god_index* idx, const uint8_t* d_reads, const uint64_t* d_
   if (total == 0) return GOD_OK;
 
   // ---- fill + sort per read
-  const uint64_t n_tiny = hf[0], n_small = hf[1], n_medium = hf[2], n_large = hf[3], n_huge = hf[4];
+  const uint64_t n_tiny = hf[0], n_small = hf[1], n_warp = hf[2], n_medium = hf[3], n_large = hf[4],
+                 n_huge = hf[5];
   if (n_tiny)
     GOD_LAUNCH(fill_sort_tiny, grid_for(n_tiny, kT, 64), kT, 0, st, sets, src.p, seed_seg.p, read_off.p, ltiny.p,
                (uint32_t)n_tiny, idx->d_ent, out);
   if (n_small)
     GOD_LAUNCH(fill_sort_small, grid_for(n_small * 32, kT, 64), kT, 0, st, sets, src.p, seed_seg.p, read_off.p,
                lsmall.p, (uint32_t)n_small, idx->d_ent, out);
+  if (n_warp)
+    GOD_LAUNCH(fill_sort_warp, grid_for(n_warp * 32, kT, 64), kT, 0, st, sets, src.p, seed_seg.p, read_off.p, lwarp.p,
+               (uint32_t)n_warp, idx->d_ent, out);
   if (n_medium)
     GOD_LAUNCH(fill_sort_medium, (unsigned)std::min<uint64_t>(n_medium, (uint64_t)num_sms() * 16), kMedThreads, 0,
                st, sets, src.p, seed_seg.p, read_off.p, lmedium.p, (uint32_t)n_medium, idx->d_ent, out);
   if (n_large + n_huge) {
     // huge reads: one task per kLargeCap-anchor tile, two merge buffers per
     // read in tmp (at twice its anchor offset), ceil(log2(most tiles)) levels
-    const uint64_t n_tasks = hf[5], most = hf[6];
+    const uint64_t n_tasks = hf[6], most = hf[7];
     if (n_tasks >= (1ull << 31)) {
       set_error("seed: too many long anchor lists in one call");
       return GOD_ERANGE;
