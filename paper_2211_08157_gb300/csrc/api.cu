@@ -391,6 +391,7 @@ uint64_t god_launch_count(void) { return g_launches.load(); }
 
 void god_set_graphs(int on) { g_graphs_on.store(on ? 1 : 0); }
 
+// Called with g_prof_mu held.
 static void prof_mark_base() {
   if (!g_prof_base && cudaEventCreate(&g_prof_base) != cudaSuccess) {
     cudaGetLastError();
@@ -401,8 +402,12 @@ static void prof_mark_base() {
 }
 
 void god_prof_enable(int on) {
-  if (!on) prof_collect();
-  else if (!g_prof_base) prof_mark_base();
+  if (!on) {
+    prof_collect();
+  } else {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (!g_prof_base) prof_mark_base();
+  }
   g_prof_on.store(on == 2 ? 2 : (on ? 1 : 0));
 }
 
