@@ -81,3 +81,19 @@ def test_seeding_entry_points_reject_null_arguments():
     cnt = np.zeros(4, np.uint32)
     first = np.zeros(4, np.uint64)
     assert L.god_index_lookup(None, keys.ctypes.data, 4, 0, cnt.ctypes.data, first.ctypes.data, None) == -1
+
+
+def test_profile_reports_empty_without_timing():
+    """The profile report and the launch timeline are host-side queries: with
+    nothing timed they are an empty object and an empty list, and the
+    size-query convention (return the needed size when cap is too small)
+    holds."""
+    import pytest
+    import paper_2211_08157_gb300 as god
+    L = _lib.load()
+    if god.god_prof_report() or god.god_prof_timeline():
+        pytest.skip("launches were timed earlier in this process")
+    need = L.god_prof_timeline(None, 0)
+    assert need == 3   # "[]" and its terminator
+    buf = C.create_string_buffer(need)
+    assert L.god_prof_timeline(buf, need) == 0 and buf.value == b"[]"
