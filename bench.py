@@ -719,7 +719,8 @@ def main():
     # reads on the 100 Mbp reference, 100,000 ONT-like reads on the 3.1 Gbp one
     workloads = None
     refs = {wl.name: ref}
-    if rank == 0 and not args.no_workloads:
+    # (the one-GPU lines: left out when several GPUs are held for the scaling run)
+    if rank == 0 and ws == 1 and not args.no_workloads:
         workloads = {}
         for wname in ("hifi_100mbp_200k", "ont_3100mbp_100k"):
             r0 = None
@@ -731,11 +732,11 @@ def main():
             workloads[wname], refs[wname] = workload_line(god, torch, dev, stream, flush, wname, r0)
 
     seed_match = None
-    if rank == 0 and not args.no_seed_match:
+    if rank == 0 and ws == 1 and not args.no_seed_match:
         seed_match = seed_match_line(god, torch, dev, stream, flush)
 
     serving = None
-    if args.serving_seconds > 0 and rank == 0:
+    if args.serving_seconds > 0 and rank == 0 and ws == 1:
         swl = synth.WORKLOADS[args.serving_workload]
         sref = refs.get(swl.name)
         if sref is None:
